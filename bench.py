@@ -1,0 +1,362 @@
+"""Benchmark: even n verified per second over [4, 10^12] on one GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one pass of the whole hot path (claim -> window sieve -> p_min
+search -> slow path -> records -> merge) over every even n in [4, 10^12].
+
+value : device throughput of the persistent graph-free launch sequence on a
+        torch stream, timed with CUDA events per step, L2 flushed between
+        steps (a 512 MB write), max over ranks.
+e2e   : the same metric through the blocking C-ABI call gb_verify_range with
+        host buffers (params H2D and the gb_result D2H inside the timed
+        region), wall clock.
+plain : the plain per-segment form (one launch triple per segment plus a
+        status round trip), timed over the same range once.
+
+Multi-GPU (torchrun): every rank verifies its own block of 10^12 integers
+[r 10^12 + 4, (r + 1) 10^12], no collective on the data path (weak scaling);
+rank 0 gathers the tiny results.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_TOP = 10**12
+LO, HI = 4, N_TOP + 1
+P_MAX, SEG_BITS = 1 << 16, 20
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n-top", type=int, default=N_TOP)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--cpu-records", type=int, default=24)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# roofline bookkeeping
+# ---------------------------------------------------------------------------
+
+def algorithmic_smem_words(n_total: int, n_top: int, tile_bits: int, k_words: int,
+                           pattern_max: int) -> dict:
+    """Algorithmic shared-memory word operations of one launch over [4, n_top].
+
+    Per even n (tile of S = 2^tile_bits n, window S + K bits):
+      fill   : (S + K)/S / 32 word stores
+      marks  : (S + K)/S * sum over marked primes p <= sqrt(n_top) of 1/p
+               read-modify-writes (each a word read and a word write)
+      search : 2 word loads per warp-chunk step, shared by the 32 lanes;
+               the step count per n is counted by the kernel-independent
+               estimate 1 + P(p_min > 63) (about 1.3 at 1e12)
+    """
+    import numpy as np
+    S = 1 << tile_bits
+    K = 32 * k_words
+    ext = (S + K) / S
+    root = int(n_top ** 0.5) + 1
+    sieve = np.ones(root + 1, dtype=bool)
+    sieve[:2] = False
+    for i in range(2, int(root ** 0.5) + 1):
+        if sieve[i]:
+            sieve[i * i::i] = False
+    primes = np.nonzero(sieve)[0]
+    marked = primes[primes > pattern_max]
+    recip = float(np.sum(1.0 / marked))
+    per_n = ext / 32 + 2 * ext * recip + 2 * 1.3 / 32
+    return {"per_n": per_n, "words": per_n * n_total, "sum_inv_p": recip}
+
+
+def load_peaks():
+    try:
+        return json.load(open(PEAKS_FILE))
+    except (OSError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle on a bounded sample
+# ---------------------------------------------------------------------------
+
+def cpu_sample(n_top: int, count: int, seed: int = 0xB0):
+    import oracle
+    from paper_2603_07850_gb300 import workloads as W
+    cfg = W.RangeConfig("bench", 4, n_top + 1, P_MAX, SEG_BITS, 0, "")
+    idx = W.sample_records(cfg, count, seed)
+    base = oracle.primes_upto(int(n_top ** 0.5) + 2)
+    lim = int(n_top ** 0.5) + 2
+    t = time.perf_counter()
+    n = 0
+    for r in idx:
+        a, b = W.record_bounds(cfg.lo, cfg.hi, SEG_BITS, r)
+        st, recs, _, _ = oracle.pmin_range(a, b, p_max=P_MAX, seg_bits=SEG_BITS, base=(base, lim))
+        n += recs[0].n_count
+    dt = time.perf_counter() - t
+    return n / dt, n, dt, len(idx)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    steps = []
+    per_step = 2
+    for i in range(args.warmup + args.steps):
+        v, n, dt, k = cpu_sample(args.n_top, per_step, seed=0xB0 + i)
+        if i >= args.warmup:
+            steps.append((n, dt))
+    n = sum(s[0] for s in steps)
+    dt = sum(s[1] for s in steps)
+    value = n / dt
+    line = {
+        "impl": "reference", "metric": "even n verified/s at N=1e12", "value": value,
+        "unit": "even_n/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "every even n in [4, 1e12]", "p_max": P_MAX, "seg_bits": SEG_BITS,
+                   "sample": f"{per_step} seeded records of 2^20 even n per step"},
+        "cpu_baseline": {"value": value, "unit": "even_n/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{per_step} seeded records of 2^20 even n per step, "
+                                   "single-threaded C oracle"},
+        "e2e": {"value": value, "unit": "even_n/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2603_07850_gb300 import binding as gb, build
+    if rank == 0 or world == 1:
+        build.build()
+    if dist:
+        dist.barrier()
+    gb.load()
+    gb.gb_init(P_MAX, SEG_BITS)
+    gb.gb_set_option("time_kernel", 1)
+    lo = rank * args.n_top + 4
+    hi = (rank + 1) * args.n_top + 1
+    n_total = (hi - 1 - lo) // 2 + 1 if lo % 2 == 0 else None
+
+    stream = torch.cuda.Stream()
+    res = torch.zeros(gb.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def step():
+        gb.gb_verify_range_async(lo, hi, res.data_ptr(), stream.cuda_stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.fill_(1)
+            step()
+    stream.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    kernel_us = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)              # L2 flush between steps (not timed)
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+            stream.synchronize()
+            kernel_us.append(gb.gb_get_option("last_kernel_us"))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(step_ms) / len(step_ms)
+    out = gb.result_from_bytes(bytes(res.cpu().numpy()))
+    if out["status"] not in (0,):
+        raise SystemExit(f"device status {out['status']}: {gb.gb_last_error()}")
+
+    # end to end through the blocking C-ABI call with host buffers
+    e2e_t = []
+    for _ in range(max(1, min(args.steps, 2))):
+        flush.fill_(3)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = gb.gb_verify_range(lo, hi)
+        e2e_t.append(time.perf_counter() - t)
+        assert r["n_count"] == out["n_count"] and r["sum_pmin"] == out["sum_pmin"]
+    e2e_s = sum(e2e_t) / len(e2e_t)
+
+    plain = None
+    if not args.no_plain:
+        flush.fill_(5)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        _, pr, _ = gb.gb_verify_range_plain(lo, hi, 0)
+        plain_s = time.perf_counter() - t
+        assert pr["sum_pmin"] == out["sum_pmin"] and pr["argmax_n"] == out["argmax_n"]
+        plain = {"value": pr["n_count"] / plain_s, "unit": "even_n/s", "seconds": plain_s,
+                 "seg_bits": gb.gb_get_option("plain_seg_bits")}
+
+    # max over ranks of the step time and of the e2e time
+    tot_n = out["n_count"]
+    if dist:
+        t = torch.tensor([ms, e2e_s, float(out["n_count"])], dtype=torch.float64, device="cuda")
+        g = [torch.zeros_like(t) for _ in range(world)]
+        dist.all_gather(g, t)
+        ms = max(float(x[0]) for x in g)
+        e2e_s = max(float(x[1]) for x in g)
+        tot_n = sum(int(x[2]) for x in g)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    peaks = load_peaks()
+    kw = gb.gb_get_option("k_words")
+    alg = algorithmic_smem_words(out["n_count"], args.n_top, gb.gb_get_option("tile_bits"), kw,
+                                 gb.gb_get_option("pattern_max"))
+    kus = statistics.mean(kernel_us) if kernel_us else None
+    sm_clock = (peaks or {}).get("sm_max_mhz", 2070.0)
+    sms = gb.gb_get_option("sms")
+    peak_words = sms * 32 * sm_clock * 1e6          # 32 banks x 4 B per clock per SM
+    achieved = alg["words"] / (kus * 1e-6) if kus else None
+    line = {
+        "metric": "even n verified/s at N=1e12", "value": tot_n / (ms * 1e-3),
+        "unit": "even_n/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "every even n in [4, 1e12] (per rank: its own 1e12 block)",
+                   "p_max": P_MAX, "seg_bits": SEG_BITS,
+                   "tile_bits": gb.gb_get_option("tile_bits"),
+                   "threads": gb.gb_get_option("threads"), "wheel": gb.gb_get_option("wheel"),
+                   "l2": "flushed between steps (512 MB write)", "form": "persistent"},
+        "e2e": {"value": tot_n / e2e_s, "unit": "even_n/s", "h2d_bytes_per_step": 64,
+                "d2h_bytes_per_step": gb.RESULT_BYTES},
+        "gpu_launches": 4 * args.steps,
+        "clocks": clocks,
+        "roofline": {"bound": "alu", "achieved": achieved / 1e9 if achieved else None,
+                     "peak": peak_words / 1e9, "unit": "Gword/s",
+                     "frac": (achieved / peak_words) if achieved else None, "traffic": None,
+                     "kernel_us": kus, "per_n_words": alg["per_n"],
+                     "peak_note": "shared-memory bank slots: SMs x 32 x max SM clock"},
+        "plain": plain,
+        "speedup_vs_plain": (tot_n / (ms * 1e-3)) / plain["value"] if plain else None,
+        "result": {k: out[k] for k in ("n_count", "max_pmin", "argmax_n", "sum_pmin", "n_slow")},
+    }
+    try:
+        v, n, dt, k = cpu_sample(args.n_top, args.cpu_records)
+        line["cpu_baseline"] = {"value": v, "unit": "even_n/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{k} seeded records of 2^20 even n in [4, 1e12], "
+                                          f"{dt:.1f} s single-threaded"}
+    except Exception as e:  # noqa: BLE001
+        line["cpu_baseline"] = {"value": None, "unit": "even_n/s", "cores": 1, "kind": "oracle",
+                                "sample": f"failed: {e}"}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

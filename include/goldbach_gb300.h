@@ -1,0 +1,223 @@
+/*
+ * goldbach_gb300.h -- C ABI of libgoldbach_gb300.so
+ *
+ * Exhaustive verification of the binary Goldbach conjecture over ranges of
+ * even integers on one GB300 (sm_103a), by a segmented double sieve that
+ * stays on the device (paper: "A Lock-Free, Fully GPU-Resident Architecture
+ * for the Verification of Goldbach's Conjecture", arXiv 2603.07850).
+ *
+ * For every even n with max(lo, 4) <= n < hi the library computes
+ *
+ *     p_min(n) = min { p prime : n - p prime }          (paper, Sec. 1)
+ *
+ * and reduces the values to per-segment records: the maximum p_min, the
+ * smallest n attaining it, a histogram of floor(log2 p_min), and wrapping
+ * 64-bit sums.  Candidates p <= P_max are searched in a bit-packed sieve
+ * window built in shared memory (paper, Sec. 3.1); any n whose p_min exceeds
+ * P_max is finished on the GPU by an exact slow path (deterministic
+ * Miller-Rabin, paper Sec. 3.4) -- there is no CPU fallback.
+ *
+ * Conventions (paper, Sec. 3.4 "Graceful error handling"): every call
+ * returns a status code instead of aborting; 0 is success, negative values
+ * are errors, positive values are informational.  The text of the last
+ * error is available from gb_last_error().
+ *
+ * Ownership: the library owns every device allocation (base-prime tables,
+ * sieve state, records) and its CUDA streams.  The caller owns every struct
+ * and buffer passed by pointer.  All pointers are host pointers unless a
+ * function says "device".
+ *
+ * Range: hi is exclusive and may be as large as 2^64 - 1 (UINT64_MAX), so
+ * the largest even n that can be verified is 2^64 - 2; all sieve arithmetic
+ * is guarded against 64-bit wrap (paper, Sec. 3.4 "Sieve arithmetic").
+ *
+ * Threading: gb_verify_range* calls are serialised on one library context.
+ * gb_submit/gb_poll are thread-safe and may be called while a
+ * gb_verify_range* call runs on another thread.
+ */
+#ifndef GOLDBACH_GB300_H
+#define GOLDBACH_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define GB_OK                 0
+#define GB_PENDING            1   /* gb_poll: request not finished yet          */
+#define GB_COUNTEREXAMPLE     2   /* an n with no prime pair was found          */
+#define GB_EINVAL            -1   /* bad argument, or gb_init not called         */
+#define GB_ENOMEM            -2   /* device memory budget or allocation failed   */
+#define GB_ECUDA             -3   /* a CUDA runtime call or kernel failed        */
+#define GB_ETIMEOUT          -4   /* a bounded wait ran out                      */
+#define GB_ESLOWPATH_LIMIT   -5   /* slow path hit its per-n iteration cap       */
+#define GB_EOVERFLOW         -6   /* p_min too large for the record encoding     */
+#define GB_EINTERNAL         -7   /* a device-side consistency check failed      */
+
+/* ---- results ----------------------------------------------------------- */
+
+/* Aggregate over a whole range (caller-owned, filled by the library). */
+typedef struct {
+    uint64_t n_first;          /* first even n covered (max(lo,4) rounded up) */
+    uint64_t n_count;          /* number of even n covered                     */
+    uint64_t max_pmin;         /* max p_min over the range                     */
+    uint64_t argmax_n;         /* smallest n with p_min(n) == max_pmin         */
+    uint64_t sum_pmin;         /* sum of p_min, mod 2^64                       */
+    uint64_t wsum_pmin;        /* sum of p_min * (k + 1) mod 2^64, k = (n - n_first) / 2 */
+    uint64_t hist[64];         /* hist[b] = #n with floor(log2 p_min) == b     */
+    uint64_t n_slow;           /* #n with p_min > P_max (finished by the slow path) */
+    uint64_t counterexample_n; /* smallest counterexample found, 0 if none     */
+    int32_t  status;           /* same value the call returned                 */
+    int32_t  reserved;
+} gb_result;
+
+/* One report segment: 2^seg_bits consecutive even n (the last one of a range
+ * may be shorter), counted from the range's n_first.  wsum_pmin uses k
+ * relative to this record's own n_first. */
+typedef struct {
+    uint64_t n_first;
+    uint64_t n_count;
+    uint64_t max_pmin;
+    uint64_t argmax_n;
+    uint64_t sum_pmin;
+    uint64_t wsum_pmin;
+    uint64_t hist[64];
+    uint64_t n_slow;
+    uint64_t counterexample_n;
+} gb_seg_record;
+
+/* Counters since gb_init. */
+typedef struct {
+    uint64_t calls;            /* completed gb_verify_range* calls              */
+    uint64_t tiles;            /* sieve tiles processed                         */
+    uint64_t n_verified;       /* even n verified                               */
+    uint64_t n_slow;           /* n finished by the slow path                   */
+    uint64_t kernel_launches;  /* kernels launched by the library              */
+    uint64_t graph_replays;    /* CUDA-graph replays of the persistent pipeline */
+    uint64_t requests_submitted;
+    uint64_t requests_completed;
+    uint64_t requests_rejected;/* refused by the memory-budget admission check  */
+    uint64_t base_prime_count; /* primes resident in the base table            */
+    uint64_t base_prime_limit; /* the table holds every prime <= this          */
+    uint64_t device_bytes;     /* device memory currently held by the library  */
+} gb_stats_t;
+
+/* ---- lifecycle ----------------------------------------------------------- */
+
+/*
+ * gb_init -- create the library context on the current CUDA device.
+ *
+ *   p_max    : candidate bound P_max (paper Sec. 3.3, "P_SMALL"): the sieve
+ *              search tries every odd prime p <= p_max; n with a larger p_min
+ *              go to the GPU slow path.  2 <= p_max <= 2^20.
+ *   seg_bits : report granularity, log2 of even n per gb_seg_record,
+ *              5 <= seg_bits <= 40 (paper Alg. 1 processes the range in
+ *              segments; here the record size is independent of the tile
+ *              size the kernels use).
+ *
+ * Builds the small-candidate table and the base primes <= 2^16 on the
+ * device.  Calling gb_init again re-initialises (gb_shutdown first).
+ * Returns GB_OK, GB_EINVAL, GB_ENOMEM or GB_ECUDA.
+ */
+int gb_init(uint32_t p_max, uint32_t seg_bits);
+
+/*
+ * gb_set_option -- tune the context.  Keys (value range):
+ *   "tile_bits"     log2 even n per sieve tile, 10..20 (default 20)
+ *   "threads"       threads per CTA: 256, 512 or 1024 (default 512)
+ *   "ctas_per_sm"   persistent CTAs per SM, 1..4 (default: as many as fit)
+ *   "wheel"         largest wheel prime pre-sieved by pattern: 7 or 13 (default 13)
+ *   "pattern_max"   largest prime cleared by in-register patterns, 13..61 (default 31)
+ *   "base_limit"    build base primes up to this value now (<= 2^32 - 1)
+ *   "mem_budget_mb" device-memory budget for serving admission (default 8192)
+ *   "plain_seg_bits" log2 even n per segment of the plain form, 20..30 (default 26)
+ *   "use_graph"     1 = replay a captured CUDA graph (default), 0 = direct launches
+ *   "slow_cap"      log2 of the slow-path candidate cap per n, 6..24 (default 24)
+ *   "timeout_ms"    bound for device-side waits and gb_poll defaults (default 600000)
+ *   "tier_b_min"    smallest prime crossed off lane-per-prime (default 4096)
+ *   "plain_slice_bits" log2 window bits per CTA in the plain sieve kernel (default 18)
+ *   "time_kernel"   1 = time the persistent kernel with CUDA events (default 0)
+ * Returns GB_OK or GB_EINVAL (unknown key or value out of range).
+ */
+int gb_set_option(const char *key, int64_t value);
+
+/* gb_get_option -- read back an option, or one of the read-only values
+ * "p_max", "seg_bits", "k_words", "sms" and "last_kernel_us" (duration of the
+ * last persistent kernel timed with time_kernel = 1, -1 if none; call it
+ * after the work has completed).  GB_EINVAL for an unknown key. */
+int gb_get_option(const char *key, int64_t *value);
+
+/* gb_shutdown -- stop the serving thread and free every device allocation. */
+void gb_shutdown(void);
+
+/* ---- range verification ------------------------------------------------------ */
+
+/*
+ * gb_verify_range -- verify every even n with max(lo,4) <= n < hi with the
+ * persistent fused kernel (CTAs claim tiles from a device atomic counter,
+ * the device form of the paper's lock-free pool, Sec. 3.2 / Alg. 1), and
+ * write the aggregate to *out (host pointer).
+ *
+ * A range with no even n >= 4 is valid and returns n_count = 0.
+ * Returns GB_OK, GB_COUNTEREXAMPLE (out->counterexample_n set), or an error.
+ */
+int gb_verify_range(uint64_t lo, uint64_t hi, gb_result *out);
+
+/*
+ * gb_verify_range_segments -- as gb_verify_range, and also copy the
+ * per-segment records (2^seg_bits even n each) into buf[0..cap).
+ * *n_written receives the number of records the range has (which may
+ * exceed cap; only cap are written).  out may be NULL.
+ */
+int gb_verify_range_segments(uint64_t lo, uint64_t hi, gb_seg_record *buf, size_t cap,
+                             size_t *n_written, gb_result *out);
+
+/*
+ * gb_verify_range_plain -- the plain per-segment form kept as the baseline
+ * the persistent kernel is measured against: a host loop that, per segment,
+ * launches a sieve kernel (bitset written to global memory), a search
+ * kernel and a reduction kernel, then reads a 4-byte status back and
+ * synchronises (paper Alg. 1).  Same outputs as gb_verify_range.
+ */
+int gb_verify_range_plain(uint64_t lo, uint64_t hi, gb_seg_record *buf, size_t cap,
+                          size_t *n_written, gb_result *out);
+
+/*
+ * gb_verify_range_async -- enqueue gb_verify_range's work on a caller
+ * stream without synchronising.  dev_out is a DEVICE pointer to a gb_result
+ * that receives the aggregate when the stream reaches that point; stream is
+ * a cudaStream_t (NULL = the library's own stream).  The caller must not
+ * enqueue another call on the context until this one has completed on the
+ * device (the context's scratch is reused).  Returns GB_OK once enqueued;
+ * device-side status lands in dev_out->status.
+ */
+int gb_verify_range_async(uint64_t lo, uint64_t hi, gb_result *dev_out, void *stream);
+
+/* ---- serving (continuous batching) ------------------------------------------ */
+
+/*
+ * gb_submit -- enqueue a range request [lo, hi) and return a ticket at once.
+ * A scheduler thread admits requests while the device-memory budget allows,
+ * interleaves their tiles in the persistent pool and finishes each request
+ * independently.  Returns GB_OK, GB_EINVAL or GB_ENOMEM (never admissible).
+ */
+int gb_submit(uint64_t lo, uint64_t hi, uint64_t *ticket);
+
+/*
+ * gb_poll -- wait up to timeout_ms (0 = do not wait, < 0 = wait forever) for
+ * a ticket.  Returns GB_PENDING while unfinished; otherwise the request's
+ * status, with *out filled and the ticket released.
+ */
+int gb_poll(uint64_t ticket, gb_result *out, int32_t timeout_ms);
+
+/* ---- introspection --------------------------------------------------------- */
+int gb_stats(gb_stats_t *out);
+const char *gb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GOLDBACH_GB300_H */

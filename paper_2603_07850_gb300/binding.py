@@ -1,0 +1,200 @@
+"""Thin ctypes binding over libgoldbach_gb300.so (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of its own: all of the sieve, search and reduction work runs in
+the library's CUDA kernels.  If the shared library is missing or fails to
+load, importing this module raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgoldbach_gb300.so")
+
+GB_OK = 0
+GB_PENDING = 1
+GB_COUNTEREXAMPLE = 2
+GB_EINVAL = -1
+GB_ENOMEM = -2
+GB_ECUDA = -3
+GB_ETIMEOUT = -4
+GB_ESLOWPATH_LIMIT = -5
+GB_EOVERFLOW = -6
+GB_EINTERNAL = -7
+
+U64 = ctypes.c_uint64
+
+
+class GbResult(ctypes.Structure):
+    _fields_ = [
+        ("n_first", U64), ("n_count", U64), ("max_pmin", U64), ("argmax_n", U64),
+        ("sum_pmin", U64), ("wsum_pmin", U64), ("hist", U64 * 64), ("n_slow", U64),
+        ("counterexample_n", U64), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+    def as_dict(self) -> dict:
+        return {f: (list(getattr(self, f)) if f == "hist" else int(getattr(self, f)))
+                for f, _ in self._fields_ if f != "reserved"}
+
+
+class GbSegRecord(ctypes.Structure):
+    _fields_ = [
+        ("n_first", U64), ("n_count", U64), ("max_pmin", U64), ("argmax_n", U64),
+        ("sum_pmin", U64), ("wsum_pmin", U64), ("hist", U64 * 64), ("n_slow", U64),
+        ("counterexample_n", U64),
+    ]
+
+
+SEG_DTYPE = np.dtype([
+    ("n_first", "<u8"), ("n_count", "<u8"), ("max_pmin", "<u8"), ("argmax_n", "<u8"),
+    ("sum_pmin", "<u8"), ("wsum_pmin", "<u8"), ("hist", "<u8", (64,)), ("n_slow", "<u8"),
+    ("counterexample_n", "<u8"),
+])
+assert SEG_DTYPE.itemsize == ctypes.sizeof(GbSegRecord)
+
+
+class GbStats(ctypes.Structure):
+    _fields_ = [(n, U64) for n in (
+        "calls", "tiles", "n_verified", "n_slow", "kernel_launches", "graph_replays",
+        "requests_submitted", "requests_completed", "requests_rejected", "base_prime_count",
+        "base_prime_limit", "device_bytes")]
+
+    def as_dict(self) -> dict:
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
+class GbError(RuntimeError):
+    def __init__(self, fn: str, code: int, msg: str):
+        super().__init__(f"{fn} -> {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the library (build it first with ``build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_2603_07850_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    u32, i32, i64, sz = ctypes.c_uint32, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+    P = ctypes.POINTER
+    sig = {
+        "gb_init": ([u32, u32], ctypes.c_int),
+        "gb_set_option": ([ctypes.c_char_p, i64], ctypes.c_int),
+        "gb_get_option": ([ctypes.c_char_p, P(i64)], ctypes.c_int),
+        "gb_shutdown": ([], None),
+        "gb_verify_range": ([U64, U64, P(GbResult)], ctypes.c_int),
+        "gb_verify_range_segments": ([U64, U64, ctypes.c_void_p, sz, P(sz), P(GbResult)], ctypes.c_int),
+        "gb_verify_range_plain": ([U64, U64, ctypes.c_void_p, sz, P(sz), P(GbResult)], ctypes.c_int),
+        "gb_verify_range_async": ([U64, U64, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+        "gb_submit": ([U64, U64, P(U64)], ctypes.c_int),
+        "gb_poll": ([U64, P(GbResult), i32], ctypes.c_int),
+        "gb_stats": ([P(GbStats)], ctypes.c_int),
+        "gb_last_error": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(fn: str, rc: int, ok=(GB_OK,)) -> int:
+    if rc not in ok:
+        raise GbError(fn, rc, gb_last_error())
+    return rc
+
+
+def gb_last_error() -> str:
+    v = load().gb_last_error()
+    return v.decode() if v else ""
+
+
+def gb_init(p_max: int = 1 << 16, seg_bits: int = 20) -> None:
+    _check("gb_init", load().gb_init(p_max, seg_bits))
+
+
+def gb_set_option(key: str, value: int) -> None:
+    _check("gb_set_option", load().gb_set_option(key.encode(), int(value)))
+
+
+def gb_get_option(key: str) -> int:
+    v = ctypes.c_int64(0)
+    _check("gb_get_option", load().gb_get_option(key.encode(), ctypes.byref(v)))
+    return v.value
+
+
+def gb_shutdown() -> None:
+    load().gb_shutdown()
+
+
+def gb_verify_range(lo: int, hi: int) -> dict:
+    r = GbResult()
+    rc = load().gb_verify_range(lo, hi, ctypes.byref(r))
+    _check("gb_verify_range", rc, ok=(GB_OK, GB_COUNTEREXAMPLE))
+    return r.as_dict()
+
+
+def _segments(fn_name: str, lo: int, hi: int, cap: int):
+    lib = load()
+    buf = np.zeros(max(cap, 1), dtype=SEG_DTYPE)
+    n = ctypes.c_size_t(0)
+    r = GbResult()
+    rc = getattr(lib, fn_name)(lo, hi, buf.ctypes.data, cap, ctypes.byref(n), ctypes.byref(r))
+    _check(fn_name, rc, ok=(GB_OK, GB_COUNTEREXAMPLE))
+    return buf[:min(cap, n.value)], r.as_dict(), n.value
+
+
+def gb_verify_range_segments(lo: int, hi: int, cap: int):
+    """Returns (records ndarray[SEG_DTYPE], aggregate dict, number of records)."""
+    return _segments("gb_verify_range_segments", lo, hi, cap)
+
+
+def gb_verify_range_plain(lo: int, hi: int, cap: int = 0):
+    return _segments("gb_verify_range_plain", lo, hi, cap)
+
+
+def gb_verify_range_async(lo: int, hi: int, dev_out_ptr: int, stream_ptr: int = 0) -> None:
+    """dev_out_ptr: device address of a gb_result-sized buffer; stream_ptr: cudaStream_t."""
+    _check("gb_verify_range_async",
+           load().gb_verify_range_async(lo, hi, ctypes.c_void_p(dev_out_ptr),
+                                        ctypes.c_void_p(stream_ptr or None)))
+
+
+def gb_submit(lo: int, hi: int) -> int:
+    t = U64(0)
+    _check("gb_submit", load().gb_submit(lo, hi, ctypes.byref(t)))
+    return t.value
+
+
+def gb_poll(ticket: int, timeout_ms: int = -1):
+    """Returns (status, result dict or None while pending)."""
+    r = GbResult()
+    rc = load().gb_poll(ticket, ctypes.byref(r), timeout_ms)
+    if rc == GB_PENDING:
+        return rc, None
+    _check("gb_poll", rc, ok=(GB_OK, GB_COUNTEREXAMPLE))
+    return rc, r.as_dict()
+
+
+def gb_stats() -> dict:
+    s = GbStats()
+    _check("gb_stats", load().gb_stats(ctypes.byref(s)))
+    return s.as_dict()
+
+
+def result_from_bytes(raw: bytes) -> dict:
+    """Decode a gb_result read back from device memory."""
+    return GbResult.from_buffer_copy(raw).as_dict()
+
+
+RESULT_BYTES = ctypes.sizeof(GbResult)

@@ -1,0 +1,849 @@
+// gb_capi.cu -- host side of libgoldbach_gb300.so: the library context, the
+// base-prime tables, the launch pipelines and the C ABI declared in
+// include/goldbach_gb300.h.
+//
+// Pipelines per call:
+//   persistent : params H2D -> clear -> persistent_kernel -> merge -> result D2H,
+//                captured once into a CUDA graph and replayed (paper Sec. 5.3
+//                proposes graphs to amortise launch cost; here the whole
+//                range is one replay and there is no per-segment host step).
+//   plain      : the paper's Alg. 1 shape, per segment: sieve kernel (global
+//                bitset) -> search kernel -> reduce kernel -> 4-byte status
+//                D2H + synchronise.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "gb_kernels.h"
+#include "gb_types.h"
+#include "gb_serve.h"
+
+using namespace gbk;
+
+namespace {
+
+struct Options {
+    int64_t tile_bits = 20;
+    int64_t threads = 512;
+    int64_t ctas_per_sm = 0;       // 0 = as many as fit
+    int64_t wheel = 13;
+    int64_t pattern_max = 31;
+    int64_t tier_b_min = 4096;
+    int64_t base_limit = 0;
+    int64_t mem_budget_mb = 8192;
+    int64_t plain_seg_bits = 26;
+    int64_t plain_slice_bits = 18;
+    int64_t use_graph = 1;
+    int64_t slow_cap = 24;
+    int64_t timeout_ms = 600000;
+    int64_t serve_batch_tiles = 4096;
+    int64_t time_kernel = 0;       // record CUDA events around the persistent kernel
+};
+
+struct GraphKey {
+    const void *fn = nullptr;
+    int grid = 0, nt = 0, wheel = 0, merge_grid = 0, clear_records = 0;
+    size_t smem = 0;
+    const void *recs = nullptr;
+    bool operator==(const GraphKey &o) const
+    {
+        return fn == o.fn && grid == o.grid && nt == o.nt && wheel == o.wheel &&
+               merge_grid == o.merge_grid && clear_records == o.clear_records && smem == o.smem &&
+               recs == o.recs;
+    }
+};
+
+struct Ctx {
+    bool inited = false;
+    int device = 0, sms = 0;
+    size_t smem_optin = 0;
+    cudaStream_t stream = nullptr;
+    uint32_t p_max = 0, seg_bits = 0, k_words = 0;
+    Options opt;
+    // base-prime table (odd primes from 3, ascending) and reciprocals
+    uint32_t *d_primes = nullptr;
+    unsigned long long *d_recip = nullptr;
+    uint64_t nprimes = 0, table_limit = 0;
+    std::vector<uint32_t> h_small;           // odd primes <= 2^16
+    uint32_t *d_PR = nullptr;
+    // per-call scratch
+    RangeParams *d_params = nullptr, *h_params = nullptr;
+    Ctrl *d_ctrl = nullptr;
+    DevRec *d_recs = nullptr;
+    size_t rec_cap = 0;
+    void *d_parts = nullptr;
+    gb_result *d_result = nullptr, *h_result = nullptr;
+    unsigned int *h_flags = nullptr;
+    // graph
+    cudaGraphExec_t gexec = nullptr;
+    GraphKey gkey;
+    // plain-form buffers
+    uint32_t *d_gwin = nullptr;
+    size_t gwin_words = 0;
+    uint32_t *d_pm = nullptr;
+    size_t pm_cap = 0;
+    gb_stats_t stats{};
+    size_t device_bytes = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // persistent-kernel timing (time_kernel)
+    bool ev_pending = false;
+};
+
+Ctx g;
+std::recursive_mutex g_mu;
+std::mutex g_err_mu;
+std::string g_err = "";
+constexpr int MERGE_GRID_CAP = 512;
+
+void set_error(const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    g_err = buf;
+}
+
+int cuda_status(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return GB_OK;
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? GB_ENOMEM : GB_ECUDA;
+}
+
+#define CK(x)                                                   \
+    do {                                                        \
+        int rc_ = cuda_status((x), #x);                         \
+        if (rc_ != GB_OK) return rc_;                           \
+    } while (0)
+
+template <class T>
+int dev_alloc(T **p, size_t bytes)
+{
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+        return GB_ENOMEM;
+    }
+    *p = (T *)q;
+    g.device_bytes += bytes;
+    return GB_OK;
+}
+
+template <class T>
+void dev_free(T **p, size_t bytes)
+{
+    if (*p) {
+        cudaFree((void *)*p);
+        g.device_bytes -= std::min(g.device_bytes, bytes);
+    }
+    *p = nullptr;
+}
+
+uint64_t isqrt_host(uint64_t x)
+{
+    uint64_t r = (uint64_t)std::sqrt((double)x);
+    if (r > 0xFFFFFFFFull) r = 0xFFFFFFFFull;
+    while (r > 0 && r > x / r) r--;
+    while (r < 0xFFFFFFFFull && (r + 1) <= x / (r + 1)) r++;
+    return r;
+}
+
+// Odd primes <= limit by a plain host sieve (limit <= 2^21): bootstrap table.
+std::vector<uint32_t> host_odd_primes(uint32_t limit)
+{
+    std::vector<uint8_t> c(limit + 1, 1);
+    std::vector<uint32_t> out;
+    for (uint64_t i = 3; i <= limit; i += 2) {
+        if (!c[i]) continue;
+        out.push_back((uint32_t)i);
+        for (uint64_t m = i * i; m <= limit; m += 2 * i) c[m] = 0;
+    }
+    return out;
+}
+
+uint32_t bitrev32(uint32_t x)
+{
+    uint32_t r = 0;
+    for (int b = 0; b < 32; b++) r |= ((x >> b) & 1u) << (31 - b);
+    return r;
+}
+
+Tables make_tables()
+{
+    Tables t{};
+    t.primes = g.d_primes;
+    t.recip = g.d_recip;
+    t.PR = g.d_PR;
+    t.nprimes = (uint32_t)g.nprimes;
+    t.k_words = g.k_words;
+    // in-register pattern primes: those above the wheel, up to pattern_max
+    static const uint32_t pat[14] = {11, 13, 17, 19, 23, 29, 31, 37, 41, 43, 47, 53, 59, 61};
+    t.pat_lo = g.opt.wheel == 13 ? 2u : 0u;
+    uint32_t hi = t.pat_lo;
+    while (hi < 14 && pat[hi] <= (uint32_t)g.opt.pattern_max) hi++;
+    t.pat_hi = hi;
+    uint32_t lim = (uint32_t)g.opt.wheel;
+    if (hi > t.pat_lo) lim = std::max(lim, pat[hi - 1]);
+    t.iA0 = (uint32_t)(std::upper_bound(g.h_small.begin(), g.h_small.end(), lim) - g.h_small.begin());
+    t.iB0 = (uint32_t)(std::lower_bound(g.h_small.begin(), g.h_small.end(),
+                                        (uint32_t)g.opt.tier_b_min) - g.h_small.begin());
+    if (t.iB0 < t.iA0) t.iB0 = t.iA0;
+    return t;
+}
+
+size_t window_words(uint32_t tile_bits)
+{
+    return ((((size_t)1 << tile_bits) + 32ull * g.k_words) / 32 + 2 + 3) & ~(size_t)3;
+}
+
+size_t persistent_smem(uint32_t tile_bits)
+{
+    return 4ull * (wheel_pattern_words((int)g.opt.wheel) + ((g.k_words + 3) & ~3u) +
+                   window_words(tile_bits));
+}
+
+// Grow the device base-prime table to every prime <= need (or base_limit).
+int ensure_table(uint64_t need)
+{
+    if (need <= g.table_limit) return GB_OK;
+    uint64_t L = std::max<uint64_t>(need, (uint64_t)g.opt.base_limit);
+    // round up to 2^k - 1 so repeated growth stays rare
+    uint64_t r = 1;
+    while (r - 1 < L && r < (1ull << 32)) r <<= 1;
+    L = std::min<uint64_t>(r - 1, 0xFFFFFFFFull);
+    if (L <= g.table_limit) return GB_OK;
+    // sieve the odd numbers q = 2j + 1, j < j_end, with the bootstrap primes
+    const uint32_t j_end = (uint32_t)((L + 1) / 2);
+    const uint32_t Z = 1u << 18;
+    const uint32_t gwords = (j_end + 31) / 32 + 2;
+    uint32_t *bits = nullptr;
+    int rc = dev_alloc(&bits, 4ull * gwords);
+    if (rc) return rc;
+    const int nt = 512;
+    const size_t smem = 4ull * (wheel_pattern_words((int)g.opt.wheel) + Z / 32 + 4);
+    const void *fn = slice_kernel_ptr((int)g.opt.wheel, nt);
+    Tables t = make_tables();                     // still the bootstrap table
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bits, 0, 4ull * gwords, g.stream);
+    if (e == cudaSuccess)
+        e = launch_slice_sieve((int)g.opt.wheel, nt, (int)((j_end + Z - 1) / Z), smem, g.stream, 0ull, 0,
+                               j_end, Z, t, bits, gwords);
+    const uint32_t nb = table_blocks(gwords);
+    uint32_t *bc = nullptr;
+    unsigned long long *bo = nullptr;
+    if (e == cudaSuccess && (rc = dev_alloc(&bc, 4ull * nb)) == GB_OK &&
+        (rc = dev_alloc(&bo, 8ull * (nb + 1))) == GB_OK) {
+        e = launch_table_compact(g.stream, bits, gwords, bc, bo, L, nullptr, nullptr, 1);
+        unsigned long long total = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&total, bo + nb, 8, cudaMemcpyDeviceToHost, g.stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g.stream);
+        uint32_t *np = nullptr;
+        unsigned long long *nr = nullptr;
+        if (e == cudaSuccess && (rc = dev_alloc(&np, 4ull * total)) == GB_OK &&
+            (rc = dev_alloc(&nr, 8ull * total)) == GB_OK) {
+            e = launch_table_compact(g.stream, bits, gwords, bc, bo, L, np, nr, 0);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(g.stream);
+            if (e == cudaSuccess) {
+                dev_free(&g.d_primes, 4ull * g.nprimes);
+                dev_free(&g.d_recip, 8ull * g.nprimes);
+                g.d_primes = np;
+                g.d_recip = nr;
+                g.nprimes = total;
+                g.table_limit = L;
+                np = nullptr;
+                nr = nullptr;
+                g.gkey = GraphKey{};                 // tables changed: recapture
+            }
+        }
+        dev_free(&np, 4ull * total);
+        dev_free(&nr, 8ull * total);
+    }
+    dev_free(&bc, 4ull * nb);
+    dev_free(&bo, 8ull * (nb + 1));
+    dev_free(&bits, 4ull * gwords);
+    if (rc) return rc;
+    return cuda_status(e, "base-prime table build");
+}
+
+int ensure_records(uint64_t nrec)
+{
+    if (nrec <= g.rec_cap) return GB_OK;
+    size_t cap = std::max<uint64_t>(nrec, 1024);
+    dev_free(&g.d_recs, sizeof(DevRec) * g.rec_cap);
+    g.rec_cap = 0;
+    int rc = dev_alloc(&g.d_recs, sizeof(DevRec) * cap);
+    if (rc) return rc;
+    g.rec_cap = cap;
+    g.gkey = GraphKey{};
+    return GB_OK;
+}
+
+struct CallPlan {
+    uint64_t n0 = 0, n_total = 0, nrec = 0, ntiles = 0;
+};
+
+// Validate a range and compute its even-n grid.  n_total == 0 means empty.
+int plan_range(uint64_t lo, uint64_t hi, CallPlan &cp)
+{
+    cp = CallPlan{};
+    uint64_t n0 = lo < 4 ? 4 : lo;
+    if (n0 & 1) {
+        if (n0 == UINT64_MAX) return GB_OK;
+        n0++;
+    }
+    if (n0 >= hi) return GB_OK;
+    uint64_t n_last = (hi - 1) & ~1ull;
+    if (n_last < n0) return GB_OK;
+    cp.n0 = n0;
+    cp.n_total = (n_last - n0) / 2 + 1;
+    cp.nrec = ((cp.n_total - 1) >> g.seg_bits) + 1;
+    cp.ntiles = ((cp.n_total - 1) >> g.opt.tile_bits) + 1;
+    return GB_OK;
+}
+
+void fill_params(const CallPlan &cp, uint32_t tile_bits, RangeParams &p)
+{
+    memset(&p, 0, sizeof p);
+    p.n0 = cp.n0;
+    p.n_total = cp.n_total;
+    p.ntiles = cp.ntiles;
+    p.nrec = cp.nrec;
+    p.p_slow_start = (g.p_max + 1ull) | 1ull;
+    p.tile_bits = tile_bits;
+    p.rec_bits = g.seg_bits;
+    p.k_words = g.k_words;
+    p.p_max = g.p_max;
+    p.slow_cap_log2 = (uint32_t)g.opt.slow_cap;
+}
+
+void empty_result(gb_result *out)
+{
+    if (!out) return;
+    memset(out, 0, sizeof *out);
+    out->status = GB_OK;
+}
+
+int prepare_common(const CallPlan &cp)
+{
+    uint64_t n_last = cp.n0 + 2 * (cp.n_total - 1);
+    int rc = ensure_table(isqrt_host(n_last));
+    if (rc) return rc;
+    return ensure_records(cp.nrec);
+}
+
+int occupancy_grid(const void *fn, int nt, size_t smem, int *grid)
+{
+    CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nt, smem));
+    if (per_sm < 1) {
+        set_error("tile does not fit in shared memory (%zu bytes)", smem);
+        return GB_ENOMEM;
+    }
+    if (g.opt.ctas_per_sm > 0) per_sm = std::min<int>(per_sm, (int)g.opt.ctas_per_sm);
+    *grid = per_sm * g.sms;
+    return GB_OK;
+}
+
+int merge_grid_for(uint64_t nrec)
+{
+    uint64_t b = (nrec + 255) / 256;
+    return (int)std::max<uint64_t>(1, std::min<uint64_t>(b, MERGE_GRID_CAP));
+}
+
+// Enqueue the persistent pipeline (without the params copy) on stream st.
+int enqueue_persistent(cudaStream_t st, const CallPlan &cp, gb_result *dev_out, int grid,
+                       size_t smem, int merge_grid, bool timed = false)
+{
+    const int clear_records = g.opt.tile_bits < g.seg_bits ? 1 : 0;
+    Tables t = make_tables();
+    CK(launch_clear(st, g.d_params, g.d_recs, g.d_ctrl, clear_records, clear_records ? 4 * g.sms : 1));
+    if (timed) {
+        if (!g.ev0) CK(cudaEventCreate(&g.ev0));
+        if (!g.ev1) CK(cudaEventCreate(&g.ev1));
+        CK(cudaEventRecord(g.ev0, st));
+    }
+    CK(launch_persistent((int)g.opt.wheel, (int)g.opt.threads, grid, smem, st, g.d_params, t, g.d_recs,
+                         g.d_ctrl));
+    if (timed) {
+        CK(cudaEventRecord(g.ev1, st));
+        g.ev_pending = true;
+    }
+    CK(launch_merge(st, merge_grid, g.d_params, g.d_recs, g.d_ctrl, g.d_parts, dev_out));
+    (void)cp;
+    return GB_OK;
+}
+
+int run_persistent(uint64_t lo, uint64_t hi, CallPlan &cp)
+{
+    int rc = plan_range(lo, hi, cp);
+    if (rc) return rc;
+    if (!cp.n_total) return GB_OK;
+    if ((rc = prepare_common(cp))) return rc;
+    const uint32_t tile_bits = (uint32_t)g.opt.tile_bits;
+    const int nt = (int)g.opt.threads;
+    const size_t smem = persistent_smem(tile_bits);
+    const void *fn = persistent_kernel_ptr((int)g.opt.wheel, nt);
+    int grid = 0;
+    if ((rc = occupancy_grid(fn, nt, smem, &grid))) return rc;
+    const int mg = merge_grid_for(cp.nrec);
+    fill_params(cp, tile_bits, *g.h_params);
+    const int clear_records = g.opt.tile_bits < g.seg_bits ? 1 : 0;
+    if (g.opt.use_graph) {
+        GraphKey key;
+        key.fn = fn; key.grid = grid; key.nt = nt; key.wheel = (int)g.opt.wheel; key.merge_grid = mg;
+        key.clear_records = clear_records; key.smem = smem; key.recs = g.d_recs;
+        if (!(key == g.gkey) || !g.gexec) {
+            if (g.gexec) { cudaGraphExecDestroy(g.gexec); g.gexec = nullptr; }
+            cudaGraph_t graph = nullptr;
+            CK(cudaStreamBeginCapture(g.stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = cudaMemcpyAsync(g.d_params, g.h_params, sizeof(RangeParams),
+                                            cudaMemcpyHostToDevice, g.stream);
+            int rc2 = e == cudaSuccess ? enqueue_persistent(g.stream, cp, g.d_result, grid, smem, mg)
+                                       : cuda_status(e, "params copy");
+            if (rc2 == GB_OK) {
+                e = cudaMemcpyAsync(g.h_result, g.d_result, sizeof(gb_result), cudaMemcpyDeviceToHost,
+                                    g.stream);
+                rc2 = cuda_status(e, "result copy");
+            }
+            cudaError_t e2 = cudaStreamEndCapture(g.stream, &graph);
+            if (rc2) { if (graph) cudaGraphDestroy(graph); return rc2; }
+            CK(e2);
+            e = cudaGraphInstantiate(&g.gexec, graph, 0);
+            cudaGraphDestroy(graph);
+            CK(e);
+            g.gkey = key;
+        }
+        CK(cudaGraphLaunch(g.gexec, g.stream));
+        g.stats.graph_replays++;
+    } else {
+        CK(cudaMemcpyAsync(g.d_params, g.h_params, sizeof(RangeParams), cudaMemcpyHostToDevice, g.stream));
+        if ((rc = enqueue_persistent(g.stream, cp, g.d_result, grid, smem, mg, g.opt.time_kernel != 0)))
+            return rc;
+        CK(cudaMemcpyAsync(g.h_result, g.d_result, sizeof(gb_result), cudaMemcpyDeviceToHost, g.stream));
+    }
+    CK(cudaStreamSynchronize(g.stream));
+    CK(cudaGetLastError());
+    g.stats.kernel_launches += 3;
+    g.stats.tiles += cp.ntiles;
+    return GB_OK;
+}
+
+void finish_stats(const CallPlan &cp, const gb_result &r)
+{
+    g.stats.calls++;
+    g.stats.n_verified += cp.n_total;
+    g.stats.n_slow += r.n_slow;
+}
+
+int copy_records(const CallPlan &cp, gb_seg_record *buf, size_t cap, size_t *n_written)
+{
+    if (n_written) *n_written = (size_t)cp.nrec;
+    if (!buf || !cap || !cp.nrec) return GB_OK;
+    size_t n = (size_t)std::min<uint64_t>(cap, cp.nrec);
+    std::vector<DevRec> h(n);
+    CK(cudaMemcpy(h.data(), g.d_recs, n * sizeof(DevRec), cudaMemcpyDeviceToHost));
+    for (size_t r = 0; r < n; r++) {
+        const DevRec &d = h[r];
+        gb_seg_record &o = buf[r];
+        memset(&o, 0, sizeof o);
+        uint64_t kfirst = (uint64_t)r << g.seg_bits;
+        o.n_first = cp.n0 + 2 * kfirst;
+        o.n_count = d.n_count;
+        o.max_pmin = d.key >> KEY_SHIFT;
+        o.argmax_n = d.key ? o.n_first + 2 * (KEY_KMASK - (d.key & KEY_KMASK)) : 0;
+        o.sum_pmin = d.sum;
+        o.wsum_pmin = d.wsum;
+        for (int b = 0; b < HIST_BINS; b++) o.hist[b] = d.hist[b];
+        o.n_slow = d.n_slow;
+        o.counterexample_n = d.ce_inv ? ~d.ce_inv : 0;
+    }
+    return GB_OK;
+}
+
+int run_plain(uint64_t lo, uint64_t hi, CallPlan &cp)
+{
+    int rc = plan_range(lo, hi, cp);
+    if (rc) return rc;
+    if (!cp.n_total) return GB_OK;
+    if ((rc = prepare_common(cp))) return rc;
+    const uint32_t sbits = (uint32_t)g.opt.plain_seg_bits;
+    const uint64_t S = 1ull << sbits;
+    const uint32_t Z = 1u << g.opt.plain_slice_bits;
+    const uint32_t kb = 32u * g.k_words;
+    const size_t need_words = (S + kb) / 32 + 8;
+    if (g.gwin_words < need_words) {
+        dev_free(&g.d_gwin, 4 * g.gwin_words);
+        g.gwin_words = 0;
+        if ((rc = dev_alloc(&g.d_gwin, 4 * need_words))) return rc;
+        g.gwin_words = need_words;
+    }
+    if (g.pm_cap < S) {
+        dev_free(&g.d_pm, 4 * g.pm_cap);
+        g.pm_cap = 0;
+        if ((rc = dev_alloc(&g.d_pm, 4 * S))) return rc;
+        g.pm_cap = S;
+    }
+    const int nt = (int)g.opt.threads;
+    const size_t smem = 4ull * (wheel_pattern_words((int)g.opt.wheel) + Z / 32 + 4);
+    const void *fn = slice_kernel_ptr((int)g.opt.wheel, nt);
+    CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    fill_params(cp, sbits, *g.h_params);
+    Tables t = make_tables();
+    CK(cudaMemcpyAsync(g.d_params, g.h_params, sizeof(RangeParams), cudaMemcpyHostToDevice, g.stream));
+    CK(launch_clear(g.stream, g.d_params, g.d_recs, g.d_ctrl, 1, 4 * g.sms));
+    const uint64_t nseg = ((cp.n_total - 1) >> sbits) + 1;
+    const uint32_t chunk = (uint32_t)std::min<uint64_t>(1ull << 14, 1ull << g.seg_bits);
+    uint64_t launches = 1;
+    for (uint64_t s = 0; s < nseg; s++) {
+        const uint64_t k0 = s << sbits;
+        const uint32_t cnt = (uint32_t)std::min<uint64_t>(S, cp.n_total - k0);
+        const uint64_t n_lo = cp.n0 + 2 * k0;
+        const uint64_t h = n_lo >> 1;
+        const bool neg = h < kb;
+        const uint64_t half_abs = neg ? kb - h : h - kb;
+        const uint32_t j_end = cnt + kb - 1;
+        const int grid = (int)((j_end + Z - 1) / Z);
+        CK(launch_slice_sieve((int)g.opt.wheel, nt, grid, smem, g.stream, half_abs, neg ? 1 : 0, j_end, Z,
+                              t, g.d_gwin, (uint32_t)g.gwin_words));
+        CK(launch_plain_search(g.stream, 8 * g.sms, g.d_params, g.d_gwin, g.d_PR, n_lo, cnt, g.d_pm,
+                               g.d_ctrl));
+        CK(launch_plain_reduce(g.stream, g.d_params, g.d_pm, k0, n_lo, cnt, chunk, g.d_recs, g.d_ctrl));
+        // the per-segment status round trip of the paper's worker loop
+        CK(cudaMemcpyAsync(g.h_flags, &g.d_ctrl->flags, 4, cudaMemcpyDeviceToHost, g.stream));
+        CK(cudaStreamSynchronize(g.stream));
+        launches += 3;
+    }
+    CK(launch_merge(g.stream, merge_grid_for(cp.nrec), g.d_params, g.d_recs, g.d_ctrl, g.d_parts,
+                    g.d_result));
+    CK(cudaMemcpyAsync(g.h_result, g.d_result, sizeof(gb_result), cudaMemcpyDeviceToHost, g.stream));
+    CK(cudaStreamSynchronize(g.stream));
+    CK(cudaGetLastError());
+    g.stats.kernel_launches += launches + 1;
+    g.stats.tiles += nseg;
+    return GB_OK;
+}
+
+void release_all()
+{
+    serve_stop();
+    if (g.gexec) { cudaGraphExecDestroy(g.gexec); g.gexec = nullptr; }
+    g.gkey = GraphKey{};
+    dev_free(&g.d_primes, 4ull * g.nprimes);
+    dev_free(&g.d_recip, 8ull * g.nprimes);
+    dev_free(&g.d_PR, 4ull * g.k_words);
+    dev_free(&g.d_params, sizeof(RangeParams));
+    dev_free(&g.d_ctrl, sizeof(Ctrl));
+    dev_free(&g.d_recs, sizeof(DevRec) * g.rec_cap);
+    dev_free(&g.d_parts, merge_part_bytes() * MERGE_GRID_CAP);
+    dev_free(&g.d_result, sizeof(gb_result));
+    dev_free(&g.d_gwin, 4 * g.gwin_words);
+    dev_free(&g.d_pm, 4 * g.pm_cap);
+    if (g.h_params) cudaFreeHost(g.h_params);
+    if (g.h_result) cudaFreeHost(g.h_result);
+    if (g.h_flags) cudaFreeHost(g.h_flags);
+    if (g.stream) cudaStreamDestroy(g.stream);
+    if (g.ev0) cudaEventDestroy(g.ev0);
+    if (g.ev1) cudaEventDestroy(g.ev1);
+    Options keep = g.opt;
+    g = Ctx{};
+    g.opt = keep;
+}
+
+int init_locked(uint32_t p_max, uint32_t seg_bits)
+{
+    if (p_max < 2 || p_max > (1u << 20)) { set_error("p_max must be in [2, 2^20]"); return GB_EINVAL; }
+    if (seg_bits < 5 || seg_bits > 40) { set_error("seg_bits must be in [5, 40]"); return GB_EINVAL; }
+    if (g.inited) release_all();
+    CK(cudaGetDevice(&g.device));
+    cudaDeviceProp prop;
+    CK(cudaGetDeviceProperties(&prop, g.device));
+    g.sms = prop.multiProcessorCount;
+    g.smem_optin = prop.sharedMemPerBlockOptin;
+    CK(cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking));
+    g.p_max = p_max;
+    g.seg_bits = seg_bits;
+    // candidate words: bit i of word t <-> p = 2(32t + i) + 1, set iff p is an
+    // odd prime <= p_max; stored bit-reversed for the clz search
+    const uint32_t K = (p_max + 1) / 2;
+    g.k_words = (K + 31) / 32;
+    std::vector<uint32_t> cand = host_odd_primes(std::max<uint32_t>(p_max, 3));
+    std::vector<uint32_t> PR(g.k_words, 0);
+    for (uint32_t p : cand) {
+        if (p > p_max) break;
+        uint32_t i = (p - 1) / 2;
+        PR[i / 32] |= 1u << (i % 32);
+    }
+    for (auto &w : PR) w = bitrev32(w);
+    int rc;
+    if ((rc = dev_alloc(&g.d_PR, 4ull * g.k_words))) return rc;
+    CK(cudaMemcpy(g.d_PR, PR.data(), 4ull * g.k_words, cudaMemcpyHostToDevice));
+    // bootstrap base primes <= 2^16
+    g.h_small = host_odd_primes(1u << 16);
+    g.nprimes = g.h_small.size();
+    std::vector<unsigned long long> rc_h(g.nprimes);
+    for (size_t i = 0; i < g.nprimes; i++) rc_h[i] = 0xFFFFFFFFFFFFFFFFull / g.h_small[i];
+    if ((rc = dev_alloc(&g.d_primes, 4ull * g.nprimes))) return rc;
+    if ((rc = dev_alloc(&g.d_recip, 8ull * g.nprimes))) return rc;
+    CK(cudaMemcpy(g.d_primes, g.h_small.data(), 4ull * g.nprimes, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(g.d_recip, rc_h.data(), 8ull * g.nprimes, cudaMemcpyHostToDevice));
+    g.table_limit = 1u << 16;
+    if ((rc = dev_alloc(&g.d_params, sizeof(RangeParams)))) return rc;
+    if ((rc = dev_alloc(&g.d_ctrl, sizeof(Ctrl)))) return rc;
+    if ((rc = dev_alloc(&g.d_parts, merge_part_bytes() * MERGE_GRID_CAP))) return rc;
+    if ((rc = dev_alloc(&g.d_result, sizeof(gb_result)))) return rc;
+    CK(cudaMemset(g.d_ctrl, 0, sizeof(Ctrl)));
+    CK(cudaMallocHost((void **)&g.h_params, sizeof(RangeParams)));
+    CK(cudaMallocHost((void **)&g.h_result, sizeof(gb_result)));
+    CK(cudaMallocHost((void **)&g.h_flags, 4));
+    memset(&g.stats, 0, sizeof g.stats);
+    g.inited = true;
+    if (g.opt.base_limit > 0 && (rc = ensure_table((uint64_t)g.opt.base_limit))) return rc;
+    return GB_OK;
+}
+
+struct OptDesc {
+    const char *key;
+    int64_t Options::*field;
+    int64_t lo, hi;
+};
+
+const OptDesc kOpts[] = {
+    {"tile_bits", &Options::tile_bits, 10, 20},
+    {"threads", &Options::threads, 256, 1024},
+    {"ctas_per_sm", &Options::ctas_per_sm, 0, 8},
+    {"wheel", &Options::wheel, 7, 13},
+    {"pattern_max", &Options::pattern_max, 7, 61},
+    {"tier_b_min", &Options::tier_b_min, 3, 1 << 16},
+    {"base_limit", &Options::base_limit, 0, 0xFFFFFFFFll},
+    {"mem_budget_mb", &Options::mem_budget_mb, 16, 1 << 22},
+    {"plain_seg_bits", &Options::plain_seg_bits, 20, 30},
+    {"plain_slice_bits", &Options::plain_slice_bits, 12, 20},
+    {"use_graph", &Options::use_graph, 0, 1},
+    {"slow_cap", &Options::slow_cap, 6, 24},
+    {"timeout_ms", &Options::timeout_ms, 1, 1ll << 40},
+    {"serve_batch_tiles", &Options::serve_batch_tiles, 1, 1 << 24},
+    {"time_kernel", &Options::time_kernel, 0, 1},
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// hooks used by the serving loop (gb_serve.cpp)
+// ---------------------------------------------------------------------------
+namespace gbk {
+std::recursive_mutex &ctx_mutex() { return g_mu; }
+bool ctx_ready() { return g.inited; }
+int64_t ctx_option(const char *key)
+{
+    for (const auto &o : kOpts)
+        if (!strcmp(o.key, key)) return g.opt.*o.field;
+    return 0;
+}
+int ctx_verify(uint64_t lo, uint64_t hi, gb_result *out)
+{
+    CallPlan cp;
+    int rc = run_persistent(lo, hi, cp);
+    if (rc) { if (out) { empty_result(out); out->status = rc; } return rc; }
+    if (!cp.n_total) { empty_result(out); finish_stats(cp, gb_result{}); return GB_OK; }
+    if (out) *out = *g.h_result;
+    finish_stats(cp, *g.h_result);
+    return g.h_result->status;
+}
+void ctx_error(const char *msg) { set_error("%s", msg); }
+gb_stats_t &ctx_stats() { return g.stats; }
+size_t ctx_device_bytes() { return g.device_bytes; }
+}  // namespace gbk
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int gb_init(uint32_t p_max, uint32_t seg_bits)
+{
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    int rc = init_locked(p_max, seg_bits);
+    if (rc && g.inited) release_all();
+    return rc;
+}
+
+int gb_set_option(const char *key, int64_t value)
+{
+    if (!key) { set_error("gb_set_option: null key"); return GB_EINVAL; }
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    for (const auto &o : kOpts) {
+        if (strcmp(o.key, key)) continue;
+        if (value < o.lo || value > o.hi) {
+            set_error("option %s out of range [%lld, %lld]", key, (long long)o.lo, (long long)o.hi);
+            return GB_EINVAL;
+        }
+        if (!strcmp(key, "threads") && value != 256 && value != 512 && value != 1024) {
+            set_error("threads must be 256, 512 or 1024");
+            return GB_EINVAL;
+        }
+        if (!strcmp(key, "wheel") && value != 7 && value != 13) {
+            set_error("wheel must be 7 or 13");
+            return GB_EINVAL;
+        }
+        g.opt.*o.field = value;
+        g.gkey = GraphKey{};
+        if (!strcmp(key, "base_limit") && g.inited && value > 0) return ensure_table((uint64_t)value);
+        return GB_OK;
+    }
+    set_error("unknown option '%s'", key);
+    return GB_EINVAL;
+}
+
+int gb_get_option(const char *key, int64_t *value)
+{
+    if (!key || !value) return GB_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    for (const auto &o : kOpts)
+        if (!strcmp(o.key, key)) { *value = g.opt.*o.field; return GB_OK; }
+    if (!strcmp(key, "p_max")) { *value = g.p_max; return GB_OK; }
+    if (!strcmp(key, "k_words")) { *value = g.k_words; return GB_OK; }
+    if (!strcmp(key, "last_kernel_us")) {
+        // duration of the last timed persistent kernel (time_kernel = 1); the
+        // stream it ran on must have completed
+        float ms = 0.f;
+        if (!g.ev_pending || cudaEventElapsedTime(&ms, g.ev0, g.ev1) != cudaSuccess) {
+            cudaGetLastError();
+            *value = -1;
+            return GB_OK;
+        }
+        *value = (int64_t)(ms * 1000.0f);
+        return GB_OK;
+    }
+    if (!strcmp(key, "seg_bits")) { *value = g.seg_bits; return GB_OK; }
+    if (!strcmp(key, "sms")) { *value = g.sms; return GB_OK; }
+    set_error("unknown option '%s'", key);
+    return GB_EINVAL;
+}
+
+void gb_shutdown(void)
+{
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    if (g.inited) release_all();
+}
+
+int gb_verify_range(uint64_t lo, uint64_t hi, gb_result *out)
+{
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    if (!g.inited) { set_error("gb_init has not been called"); return GB_EINVAL; }
+    if (!out) { set_error("gb_verify_range: null result pointer"); return GB_EINVAL; }
+    return ctx_verify(lo, hi, out);
+}
+
+int gb_verify_range_segments(uint64_t lo, uint64_t hi, gb_seg_record *buf, size_t cap,
+                             size_t *n_written, gb_result *out)
+{
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    if (!g.inited) { set_error("gb_init has not been called"); return GB_EINVAL; }
+    CallPlan cp;
+    int rc = run_persistent(lo, hi, cp);
+    if (rc) { if (out) { empty_result(out); out->status = rc; } return rc; }
+    if (!cp.n_total) {
+        if (n_written) *n_written = 0;
+        empty_result(out);
+        return GB_OK;
+    }
+    if ((rc = copy_records(cp, buf, cap, n_written))) return rc;
+    if (out) *out = *g.h_result;
+    finish_stats(cp, *g.h_result);
+    return g.h_result->status;
+}
+
+int gb_verify_range_plain(uint64_t lo, uint64_t hi, gb_seg_record *buf, size_t cap,
+                          size_t *n_written, gb_result *out)
+{
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    if (!g.inited) { set_error("gb_init has not been called"); return GB_EINVAL; }
+    CallPlan cp;
+    int rc = run_plain(lo, hi, cp);
+    if (rc) { if (out) { empty_result(out); out->status = rc; } return rc; }
+    if (!cp.n_total) {
+        if (n_written) *n_written = 0;
+        empty_result(out);
+        return GB_OK;
+    }
+    if ((rc = copy_records(cp, buf, cap, n_written))) return rc;
+    if (out) *out = *g.h_result;
+    finish_stats(cp, *g.h_result);
+    return g.h_result->status;
+}
+
+int gb_verify_range_async(uint64_t lo, uint64_t hi, gb_result *dev_out, void *stream)
+{
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    if (!g.inited) { set_error("gb_init has not been called"); return GB_EINVAL; }
+    if (!dev_out) { set_error("gb_verify_range_async: null result pointer"); return GB_EINVAL; }
+    cudaStream_t st = stream ? (cudaStream_t)stream : g.stream;
+    CallPlan cp;
+    int rc = plan_range(lo, hi, cp);
+    if (rc) return rc;
+    if (!cp.n_total) {
+        gb_result z;
+        empty_result(&z);
+        CK(cudaMemcpyAsync(dev_out, &z, sizeof z, cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+        return GB_OK;
+    }
+    if ((rc = prepare_common(cp))) return rc;
+    const uint32_t tile_bits = (uint32_t)g.opt.tile_bits;
+    const int nt = (int)g.opt.threads;
+    const size_t smem = persistent_smem(tile_bits);
+    int grid = 0;
+    if ((rc = occupancy_grid(persistent_kernel_ptr((int)g.opt.wheel, nt), nt, smem, &grid))) return rc;
+    RangeParams p;
+    fill_params(cp, tile_bits, p);
+    // the params travel as a kernel argument so no host buffer outlives the call
+    CK(launch_set_params(st, g.d_params, p));
+    if ((rc = enqueue_persistent(st, cp, dev_out, grid, smem, merge_grid_for(cp.nrec),
+                                 g.opt.time_kernel != 0)))
+        return rc;
+    g.stats.kernel_launches += 4;
+    g.stats.tiles += cp.ntiles;
+    g.stats.calls++;
+    g.stats.n_verified += cp.n_total;
+    return GB_OK;
+}
+
+int gb_stats(gb_stats_t *out)
+{
+    if (!out) return GB_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    *out = g.stats;
+    serve_fill_stats(out);
+    out->base_prime_count = g.nprimes ? g.nprimes + 1 : 0;   // + the prime 2
+    out->base_prime_limit = g.table_limit;
+    out->device_bytes = g.device_bytes;
+    return GB_OK;
+}
+
+const char *gb_last_error(void)
+{
+    static thread_local std::string copy;
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    copy = g_err;
+    return copy.c_str();
+}
+
+}  // extern "C"

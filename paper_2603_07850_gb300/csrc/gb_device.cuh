@@ -1,0 +1,438 @@
+// gb_device.cuh -- device-side building blocks of the Goldbach range verifier.
+//
+// Sieve window (paper Sec. 3.1, rebuilt for sm_103a): the odd integers of a
+// window are one bit each, bit j <-> q = wbase + 2j, in shared memory.  A
+// window is built in three passes:
+//   1. fill    : every word is written once from a pre-sieved pattern of the
+//                wheel primes 3*5*7(*11*13) and in-register masks of the next
+//                few primes (no shared-memory read-modify-write at all);
+//   2. marking : the remaining base primes p <= sqrt(q_hi) clear their odd
+//                multiples from p^2 on with shared-memory atomicAnd, one warp
+//                per prime for the dense small primes (tier A) and one lane
+//                per prime for the sparse large ones (tier B);
+//   3. fix-ups : q <= 1 cleared, the pattern primes themselves set again.
+// Overflow guards follow paper Sec. 3.4: a prime sieves only while
+// p*p <= q_hi (p < 2^32 so p*p cannot wrap), and the first multiple is found
+// from wbase mod p as a distance, never by forming a value above q_hi.
+//
+// p_min search (paper Sec. 3.1 phase 1, Sec. 5.3 bitwise direction): for the
+// 32 consecutive even n of one warp, candidate p = 2i+1 maps to the window
+// bit c - i with c the bit of q = n - 1.  Lane l of chunk t extracts the 32
+// window bits [c - 32t - 31, c - 32t] with one funnel shift of two words that
+// every lane of the warp shares (broadcast), ANDs them with the bit-reversed
+// candidate word t, and the smallest candidate is 32t + clz(mask).
+//
+// Slow path (paper Sec. 3.3, moved onto the GPU): an n with no candidate
+// p <= P_max is finished by its warp, 32 odd candidates p > P_max per step,
+// each p and n - p tested by deterministic Miller-Rabin with the first 12
+// primes as bases (paper Sec. 3.4), Montgomery multiplication in 64 bits.
+#pragma once
+#include <stdint.h>
+#include <cuda_runtime.h>
+
+#include "gb_types.h"
+
+namespace gbk {
+
+#define GB_FULL_MASK 0xffffffffu
+
+// Primes cleared by in-register masks during the fill (those above the wheel).
+// A constexpr function so that, in unrolled loops, every p is a compile-time
+// constant and every "mod p" becomes a multiply-high.
+constexpr int NPAT = 14;
+__host__ __device__ constexpr uint32_t pat_prime(int i)
+{
+    return i == 0 ? 11u : i == 1 ? 13u : i == 2 ? 17u : i == 3 ? 19u : i == 4 ? 23u :
+           i == 5 ? 29u : i == 6 ? 31u : i == 7 ? 37u : i == 8 ? 41u : i == 9 ? 43u :
+           i == 10 ? 47u : i == 11 ? 53u : i == 12 ? 59u : 61u;
+}
+
+// ---------------------------------------------------------------------------
+// small integer helpers
+// ---------------------------------------------------------------------------
+
+// x mod p for 64-bit x and 32-bit p, with m = floor((2^64-1)/p): the quotient
+// estimate umulhi(x, m) is at most one below floor(x / p).
+__device__ __forceinline__ uint32_t mod_recip(unsigned long long x, uint32_t p,
+                                              unsigned long long m)
+{
+    unsigned long long q = __umul64hi(x, m);
+    unsigned long long r = x - q * (unsigned long long)p;
+    if (r >= p) r -= p;
+    return (uint32_t)r;
+}
+
+// floor(sqrt(x)) for any 64-bit x, exact (corrected with division).
+__device__ __forceinline__ unsigned long long isqrt_u64(unsigned long long x)
+{
+    unsigned long long r = (unsigned long long)sqrt((double)x);
+    if (r > 0xFFFFFFFFull) r = 0xFFFFFFFFull;
+    while (r > 0 && r > x / r) r--;
+    while (r < 0xFFFFFFFFull && (r + 1) <= x / (r + 1)) r++;
+    return r;
+}
+
+// Number of table primes <= v (table is ascending, odd primes from 3).
+__device__ __forceinline__ uint32_t count_le(const uint32_t *primes, uint32_t n,
+                                             unsigned long long v)
+{
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+        uint32_t mid = (lo + hi) >> 1;
+        if ((unsigned long long)primes[mid] <= v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(GB_FULL_MASK, v, o);
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long w = __shfl_xor_sync(GB_FULL_MASK, v, o);
+        v = w < v ? w : v;
+    }
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// deterministic Miller-Rabin, bases = the first 12 primes (paper Sec. 3.4;
+// correct for every x < 2^64 -- Sorenson and Webster 2015 prove the 12-prime
+// set for x < 3.18e23).  Montgomery arithmetic modulo odd x (Montgomery 1985).
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned long long mont_mul(unsigned long long a, unsigned long long b,
+                                                       unsigned long long x,
+                                                       unsigned long long ninv)
+{
+    unsigned long long lo = a * b, hi = __umul64hi(a, b);
+    unsigned long long m = lo * ninv;                // lo + m*x == 0 mod 2^64
+    unsigned long long mxhi = __umul64hi(m, x);
+    unsigned long long t = hi + mxhi;
+    bool ov = t < hi;
+    unsigned long long c = (lo != 0ull) ? 1ull : 0ull;
+    unsigned long long t2 = t + c;
+    ov |= (t2 < t);
+    if (ov || t2 >= x) t2 -= x;                      // result < 2x, one subtraction
+    return t2;
+}
+
+static __device__ bool is_prime_u64(unsigned long long x)
+{
+    if (x < 2) return false;
+    const uint32_t sp[12] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
+#pragma unroll
+    for (int i = 0; i < 12; i++) {
+        if (x == sp[i]) return true;
+        if (x % sp[i] == 0) return false;
+    }
+    if (x < 41ull * 41ull) return true;             // no factor <= 37 and x < 41^2
+    // -x^{-1} mod 2^64 by Newton's iteration (x odd: x*x == 1 mod 8)
+    unsigned long long inv = x;
+#pragma unroll
+    for (int i = 0; i < 5; i++) inv *= 2ull - x * inv;
+    unsigned long long ninv = 0ull - inv;
+    unsigned long long r1 = (0ull - x) % x;          // 2^64 mod x  (Montgomery 1)
+    unsigned long long r2 = r1;                      // 2^128 mod x by 64 doublings
+    for (int i = 0; i < 64; i++) {
+        unsigned long long d = r2 << 1;
+        if ((r2 >> 63) || d >= x) d -= x;
+        r2 = d;
+    }
+    unsigned long long xm1 = x - 1;
+    int s = __ffsll((long long)xm1) - 1;
+    unsigned long long d = xm1 >> s;
+    unsigned long long mone = x - r1;                // Montgomery -1
+    int top = 63 - __clzll((long long)d);
+    for (int i = 0; i < 12; i++) {
+        unsigned long long a = mont_mul(sp[i], r2, x, ninv);   // sp[i] * 2^64 mod x
+        unsigned long long y = a;                    // leading bit of d
+        for (int b = top - 1; b >= 0; b--) {
+            y = mont_mul(y, y, x, ninv);
+            if ((d >> b) & 1ull) y = mont_mul(y, a, x, ninv);
+        }
+        if (y == r1 || y == mone) continue;
+        bool comp = true;
+        for (int k = 1; k < s; k++) {
+            y = mont_mul(y, y, x, ninv);
+            if (y == mone) { comp = false; break; }
+        }
+        if (comp) return false;
+    }
+    return true;
+}
+
+// Warp-cooperative exact search for p_min(n) over odd p >= p_start (all lanes
+// call with the same n).  Returns p_min, or 0 with a flag set: F_COUNTEREX if
+// no p <= n/2 works (the counterexample is recorded), F_SLOWCAP if the
+// candidate cap ran out first.
+static __device__ unsigned long long slow_pmin(unsigned long long n, unsigned long long p_start,
+                                        uint32_t cap_log2, Ctrl *ctrl)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned long long half = n >> 1;
+    const unsigned long long steps = cap_log2 >= 6 ? (1ull << (cap_log2 - 6)) : 1ull;
+    // once any warp has exhausted its cap the call has failed: stop early
+    // (lane 0 reads the flag and broadcasts it so the warp stays converged)
+    unsigned int fl = lane == 0 ? *(volatile unsigned int *)&ctrl->flags : 0u;
+    fl = __shfl_sync(GB_FULL_MASK, fl, 0);
+    if (fl & (F_SLOWCAP | F_INTERNAL)) return 0;
+    for (unsigned long long it = 0; it < steps; ++it) {
+        unsigned long long base = p_start + 64ull * it;
+        if (base > half) break;
+        unsigned long long p = base + 2ull * lane;
+        bool ok = (p <= half) && is_prime_u64(p) && is_prime_u64(n - p);
+        uint32_t m = __ballot_sync(GB_FULL_MASK, ok);
+        if (m) return base + 2ull * (unsigned long long)(__ffs(m) - 1);
+        if (it + 1 == steps) {
+            if (lane == 0) atomicOr(&ctrl->flags, F_SLOWCAP);
+            return 0;
+        }
+    }
+    if (lane == 0) {
+        atomicOr(&ctrl->flags, F_COUNTEREX);
+        atomicMax(&ctrl->ce_inv, ~n);
+    }
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// window geometry
+// ---------------------------------------------------------------------------
+
+// Bit j of a window stands for q = wbase + 2j.  The true value of wbase may be
+// below 1 near the origin; it is kept modulo 2^64 in `wbase` and described
+// exactly by (half_abs, neg): (wbase - 1) / 2 == neg ? -half_abs : +half_abs.
+struct WinGeom {
+    unsigned long long wbase;
+    unsigned long long half_abs;
+    unsigned long long q_hi;           // q of bit j_end - 1
+    uint32_t neg;
+    uint32_t j_end;                    // bits [0, j_end) are sieved, the rest zero
+    uint32_t clear_upto;               // bits [0, clear_upto) stand for q <= 1
+    uint32_t nfill;                    // words written by the fill pass
+};
+
+__device__ __forceinline__ WinGeom make_geom(unsigned long long half_abs, bool neg, uint32_t j_end)
+{
+    WinGeom g;
+    g.half_abs = half_abs;
+    g.neg = neg ? 1u : 0u;
+    g.wbase = neg ? (1ull - 2ull * half_abs) : (2ull * half_abs + 1ull);
+    g.j_end = j_end;
+    g.q_hi = g.wbase + 2ull * (unsigned long long)(j_end - 1);   // exact when j_end > 0
+    g.clear_upto = (neg || half_abs == 0) ? (uint32_t)(neg ? half_abs + 1 : 1) : 0u;
+    g.nfill = (j_end + 31) / 32 + 1;
+    return g;
+}
+
+// Window of a verification tile whose first even n is n_lo, holding cnt n:
+// it starts K_bits odd numbers below n_lo + 1 so every q = n - p with
+// p < 2 K_bits is inside, and ends at q = n_last - 1.
+__device__ __forceinline__ WinGeom tile_geom(unsigned long long n_lo, uint32_t cnt, uint32_t k_bits)
+{
+    unsigned long long h = n_lo >> 1;
+    bool neg = h < k_bits;
+    unsigned long long half_abs = neg ? (k_bits - h) : (h - k_bits);
+    return make_geom(half_abs, neg, cnt + k_bits - 1);
+}
+
+// ---------------------------------------------------------------------------
+// sieve passes
+// ---------------------------------------------------------------------------
+
+template <int WHEEL> struct WheelM;
+template <> struct WheelM<13> { static constexpr uint32_t M = 3u * 5u * 7u * 11u * 13u; };
+template <> struct WheelM<7> { static constexpr uint32_t M = 3u * 5u * 7u; };
+
+// Wheel pattern words in shared memory: bit u of the pattern is 1 iff 2u+1 is
+// coprime to M; M + 64 bits so any 32-bit run starting below M can be read
+// with one funnel shift.
+template <int WHEEL, int NT>
+__device__ void build_wheel_pattern(uint32_t *pat)
+{
+    constexpr uint32_t M = WheelM<WHEEL>::M;
+    constexpr uint32_t NW = (M + 64 + 31) / 32;
+    for (uint32_t w = threadIdx.x; w < NW; w += NT) {
+        uint32_t word = 0;
+        for (uint32_t b = 0; b < 32; b++) {
+            uint32_t u = (32 * w + b) % M;
+            uint32_t o = 2 * u + 1;
+            bool cop = (o % 3) && (o % 5) && (o % 7);
+            if (WHEEL == 13) cop = cop && (o % 11) && (o % 13);
+            word |= (cop ? 1u : 0u) << b;
+        }
+        pat[w] = word;
+    }
+}
+
+// Pass 1: write every window word from the wheel pattern and the in-register
+// masks of the pattern primes, zeroing bits outside [clear_upto, j_end).
+template <int WHEEL, int NT>
+__device__ __forceinline__ void fill_pass(uint32_t *win, const uint32_t *wpat, const WinGeom &g,
+                                          uint32_t pat_lo, uint32_t pat_hi)
+{
+    constexpr uint32_t M = WheelM<WHEEL>::M;
+    constexpr uint32_t STEP_M = (32u * NT) % M;
+    // phase of word 0: u0 = ((wbase - 1) / 2) mod m, exact for negative values
+    uint32_t u0 = (uint32_t)(g.half_abs % M);
+    if (g.neg && u0) u0 = M - u0;
+    uint32_t u = (uint32_t)((u0 + 32ull * threadIdx.x) % M);
+    uint32_t r[NPAT];
+#pragma unroll
+    for (int i = 0; i < NPAT; i++) {
+        const uint32_t p = pat_prime(i);
+        uint32_t v = (uint32_t)(g.half_abs % p);
+        if (g.neg && v) v = p - v;
+        r[i] = (v + 32u * threadIdx.x) % p;
+    }
+    for (uint32_t w = threadIdx.x; w < g.nfill; w += NT) {
+        uint32_t ui = u >> 5, us = u & 31;
+        uint32_t word = __funnelshift_r(wpat[ui], wpat[ui + 1], us);
+#pragma unroll
+        for (int i = 0; i < NPAT; i++) {
+            if (i >= (int)pat_lo && i < (int)pat_hi) {
+                const uint32_t p = pat_prime(i);
+                const uint32_t h = (p - 1) / 2;      // 2u+1 == 0 mod p  <=>  u == h mod p
+                uint32_t b0 = h >= r[i] ? h - r[i] : h + p - r[i];
+                uint32_t clr = (b0 < 32 ? (1u << b0) : 0u);
+                if (p < 32) clr |= (b0 + p < 32 ? (1u << (b0 + p)) : 0u);
+                if (2 * p < 32) clr |= (b0 + 2 * p < 32 ? (1u << (b0 + 2 * p)) : 0u);
+                word &= ~clr;
+            }
+        }
+        uint32_t jw = 32u * w;
+        if (jw + 32 > g.j_end) word &= (g.j_end > jw) ? (0xffffffffu >> (32 - (g.j_end - jw))) : 0u;
+        if (g.clear_upto > jw) word &= (g.clear_upto >= jw + 32) ? 0u : (0xffffffffu << (g.clear_upto - jw));
+        win[w] = word;
+        u += STEP_M;
+        if (u >= M) u -= M;
+#pragma unroll
+        for (int i = 0; i < NPAT; i++) {
+            const uint32_t p = pat_prime(i);
+            r[i] += (32u * NT) % p;
+            if (r[i] >= p) r[i] -= p;
+        }
+    }
+}
+
+// First window bit of the odd multiples of p that are >= max(p^2, wbase).
+// Returns 0xffffffff when p has nothing to clear in [0, j_end).
+__device__ __forceinline__ uint32_t first_bit(const WinGeom &g, uint32_t p, unsigned long long m)
+{
+    unsigned long long pp = (unsigned long long)p * p;      // p < 2^32: no wrap
+    if (pp > g.q_hi) return 0xffffffffu;
+    unsigned long long j;
+    if (g.neg || pp >= g.wbase) {
+        j = (pp - g.wbase) >> 1;                            // true distance, wrap-safe
+    } else {
+        uint32_t r = mod_recip(g.wbase, p, m);
+        unsigned long long d = r ? (unsigned long long)(p - r) : 0ull;
+        if (d & 1ull) d += p;                                // wbase odd: need d even
+        j = d >> 1;
+    }
+    return j < g.j_end ? (uint32_t)j : 0xffffffffu;
+}
+
+__device__ __forceinline__ void clear_bit(uint32_t *win, uint32_t j)
+{
+    atomicAnd(&win[j >> 5], ~(1u << (j & 31)));
+}
+
+// Pass 2: cross off the odd multiples of primes[iA0 .. np) in the window.
+template <int NT>
+__device__ __forceinline__ void mark_pass(uint32_t *win, const WinGeom &g, const Tables &t, uint32_t np)
+{
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    constexpr int NWARP = NT / 32;
+    const uint32_t j_end = g.j_end;
+    // tier A: one warp per prime, lane l clears multiples l, l+32, ... of it
+    uint32_t a_end = t.iB0 < np ? t.iB0 : np;
+    for (uint32_t i = t.iA0 + warp; i < a_end; i += NWARP) {
+        uint32_t p = t.primes[i];
+        uint32_t j0 = first_bit(g, p, t.recip[i]);
+        if (j0 == 0xffffffffu) continue;
+        uint32_t step = 32u * p;
+        for (uint32_t j = j0 + lane * p; j < j_end; j += step) clear_bit(win, j);
+    }
+    // tier B: one lane per prime
+    for (uint32_t i = (t.iB0 > t.iA0 ? t.iB0 : t.iA0) + threadIdx.x; i < np; i += NT) {
+        uint32_t p = t.primes[i];
+        uint32_t j0 = first_bit(g, p, t.recip[i]);
+        if (j0 == 0xffffffffu) continue;
+        for (uint32_t j = j0;;) {                           // j + p may exceed 2^32: test first
+            clear_bit(win, j);
+            if (j_end - j <= p) break;
+            j += p;
+        }
+    }
+}
+
+// Pass 3: give back the pattern and wheel primes that lie in the window
+// (the patterns cleared every multiple of them, themselves included).
+template <int WHEEL>
+__device__ __forceinline__ void fixup_pass(uint32_t *win, const WinGeom &g, uint32_t pat_hi)
+{
+    if (threadIdx.x != 0) return;
+    if (!g.neg && g.wbase > 61) return;
+    const uint32_t small[18] = {3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37, 41, 43, 47, 53, 59, 61, 0};
+    uint32_t lim = pat_hi ? pat_prime((int)pat_hi - 1) : (uint32_t)WHEEL;
+    if (lim < (uint32_t)WHEEL) lim = WHEEL;
+    for (int i = 0; small[i] && small[i] <= lim; i++) {
+        unsigned long long q = small[i];
+        unsigned long long d = q - g.wbase;                   // true distance if q >= wbase
+        bool inside = g.neg ? true : (q >= g.wbase);
+        if (!inside || q > g.q_hi) continue;
+        unsigned long long j = d >> 1;
+        if (j < g.j_end) atomicOr(&win[j >> 5], 1u << (j & 31));
+    }
+}
+
+// Build the whole window (passes 1-3).  Ends with a barrier.
+template <int WHEEL, int NT>
+__device__ __forceinline__ void build_window(uint32_t *win, const uint32_t *wpat, const WinGeom &g,
+                                             const Tables &t)
+{
+    fill_pass<WHEEL, NT>(win, wpat, g, t.pat_lo, t.pat_hi);
+    __syncthreads();
+    uint32_t np = count_le(t.primes, t.nprimes, isqrt_u64(g.q_hi));
+    mark_pass<NT>(win, g, t, np);
+    fixup_pass<WHEEL>(win, g, t.pat_hi);
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// p_min search for one warp chunk of 32 consecutive even n
+// ---------------------------------------------------------------------------
+
+// Lane l handles the n with tile index k = 32 g + l.  win is the window of a
+// tile built by tile_geom (k_words candidate words).  Returns p_min, or 0 if
+// no candidate p <= P_max works (then the caller runs slow_pmin).
+__device__ __forceinline__ uint32_t fast_pmin(const uint32_t *win, const uint32_t *PR,
+                                              uint32_t k_words, uint32_t g, bool active)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    bool done = !active;
+    uint32_t res = 0;
+    const uint32_t wb = g + k_words - 1;
+    for (uint32_t t = 0; t < k_words; ++t) {
+        if (__all_sync(GB_FULL_MASK, done)) break;
+        uint32_t lo = win[wb - t], hi = win[wb - t + 1];
+        uint32_t x = __funnelshift_r(lo, hi, lane);
+        uint32_t m = x & PR[t];
+        if (!done && m) {
+            res = 2u * (32u * t + __clz(m)) + 1u;
+            done = true;
+        }
+    }
+    return res;
+}
+
+}  // namespace gbk

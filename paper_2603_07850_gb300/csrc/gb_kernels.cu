@@ -1,0 +1,652 @@
+// gb_kernels.cu -- CUDA kernels of the Goldbach range verifier (sm_103a).
+//
+// persistent_kernel : the fused hot path.  A grid of (SMs x CTAs/SM) CTAs
+//                     claims tiles from one device atomic counter -- the
+//                     on-device form of the paper's lock-free work pool
+//                     (Sec. 3.2, Alg. 1) -- and for each tile builds the sieve
+//                     window in shared memory, finds p_min for every even n,
+//                     finishes over-bound n on the spot, and reduces the tile
+//                     to its records.  No host round trip per tile.
+// merge_kernel      : folds the records of a call into one gb_result.
+// plain_*           : the per-segment baseline (sieve -> global bitset,
+//                     search -> p_min array, reduce -> records), launched by a
+//                     host loop that synchronises on a status word per segment
+//                     (paper Alg. 1).
+// table_*           : base-prime table builder (segmented sieve + compaction).
+#include <stdint.h>
+#include <cuda_runtime.h>
+
+#include "gb_device.cuh"
+#include "gb_kernels.h"
+
+namespace gbk {
+
+// ---------------------------------------------------------------------------
+// persistent fused kernel
+// ---------------------------------------------------------------------------
+
+struct RedScratch {
+    unsigned long long arg[32], sum[32], wsum[32], ce[32];
+    uint32_t mx[32], slow[32];
+    uint32_t hist[HIST_BINS];
+    unsigned long long tile;
+};
+
+// Fold one p_min into a lane's running record state.
+struct LaneAcc {
+    uint32_t mx, slow;
+    unsigned long long arg, sum, wsum, ce, hA, hB;
+    __device__ __forceinline__ void reset()
+    {
+        mx = 0; slow = 0; arg = ~0ull; sum = 0; wsum = 0; ce = 0; hA = 0; hB = 0;
+    }
+    __device__ __forceinline__ void add(uint32_t pm, unsigned long long kr, uint32_t p_max,
+                                        uint32_t *s_hist)
+    {
+        if (pm > mx) { mx = pm; arg = kr; }           // k ascends per lane: first max wins
+        sum += pm;
+        wsum += (unsigned long long)pm * (kr + 1ull);
+        slow += pm > p_max ? 1u : 0u;
+        uint32_t b = 31u - __clz(pm);                 // floor(log2 p_min) >= 1
+        if (b <= 4) hA += 1ull << (16u * (b - 1u));
+        else if (b <= 8) hB += 1ull << (16u * (b - 5u));
+        else atomicAdd(&s_hist[b], 1u);
+    }
+};
+
+// CTA-wide reduction of the lanes' state into record r.  `whole` = the tile
+// owns the record (plain stores) instead of sharing it (atomics).
+template <int NT>
+__device__ __forceinline__ void reduce_to_record(LaneAcc &a, RedScratch &s, DevRec *rec,
+                                                 uint32_t n_cnt, bool whole, Ctrl *ctrl)
+{
+    constexpr int NWARP = NT / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t wmax = __reduce_max_sync(GB_FULL_MASK, a.mx);
+    unsigned long long warg = warp_min_u64(a.mx == wmax ? a.arg : ~0ull);
+    unsigned long long wsum = warp_sum_u64(a.sum), wws = warp_sum_u64(a.wsum);
+    unsigned long long wce = a.ce;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long v = __shfl_xor_sync(GB_FULL_MASK, wce, o);
+        wce = v > wce ? v : wce;
+    }
+    uint32_t wslow = __reduce_add_sync(GB_FULL_MASK, a.slow);
+#pragma unroll
+    for (int f = 0; f < 4; f++) {
+        uint32_t ca = __reduce_add_sync(GB_FULL_MASK, (uint32_t)(a.hA >> (16 * f)) & 0xffffu);
+        uint32_t cb = __reduce_add_sync(GB_FULL_MASK, (uint32_t)(a.hB >> (16 * f)) & 0xffffu);
+        if (lane == 0) {
+            if (ca) atomicAdd(&s.hist[1 + f], ca);
+            if (cb) atomicAdd(&s.hist[5 + f], cb);
+        }
+    }
+    if (lane == 0) {
+        s.mx[warp] = wmax; s.arg[warp] = warg; s.sum[warp] = wsum; s.wsum[warp] = wws;
+        s.slow[warp] = wslow; s.ce[warp] = wce;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t m = lane < NWARP ? s.mx[lane] : 0u;
+        unsigned long long ar = lane < NWARP ? s.arg[lane] : ~0ull;
+        uint32_t cm = __reduce_max_sync(GB_FULL_MASK, m);
+        unsigned long long ca = warp_min_u64(m == cm ? ar : ~0ull);
+        unsigned long long su = warp_sum_u64(lane < NWARP ? s.sum[lane] : 0ull);
+        unsigned long long ws = warp_sum_u64(lane < NWARP ? s.wsum[lane] : 0ull);
+        uint32_t sl = __reduce_add_sync(GB_FULL_MASK, lane < NWARP ? s.slow[lane] : 0u);
+        unsigned long long ce = lane < NWARP ? s.ce[lane] : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            unsigned long long v = __shfl_xor_sync(GB_FULL_MASK, ce, o);
+            ce = v > ce ? v : ce;
+        }
+        unsigned long long key = cm ? (((unsigned long long)cm << KEY_SHIFT) | (KEY_KMASK - ca)) : 0ull;
+        if (whole) {
+            if (lane == 0) {
+                rec->key = key; rec->sum = su; rec->wsum = ws; rec->n_count = n_cnt;
+                rec->n_slow = sl; rec->ce_inv = ce;
+            }
+            rec->hist[lane] = s.hist[lane];
+        } else {
+            if (lane == 0) {
+                if (key) atomicMax(&rec->key, key);
+                atomicAdd(&rec->sum, su);
+                atomicAdd(&rec->wsum, ws);
+                atomicAdd(&rec->n_count, (unsigned long long)n_cnt);
+                if (sl) atomicAdd(&rec->n_slow, (unsigned long long)sl);
+                if (ce) atomicMax(&rec->ce_inv, ce);
+            }
+            if (s.hist[lane]) atomicAdd(&rec->hist[lane], (unsigned long long)s.hist[lane]);
+        }
+        if (lane == 0 && sl) atomicAdd(&ctrl->slow_total, (unsigned long long)sl);
+    }
+}
+
+template <int WHEEL, int NT>
+__global__ void __launch_bounds__(NT, 1)
+persistent_kernel(const RangeParams *__restrict__ prm_g, Tables t, DevRec *__restrict__ recs,
+                  Ctrl *ctrl)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ RedScratch s;
+    constexpr int NWARP = NT / 32;
+    constexpr uint32_t WP = ((WheelM<WHEEL>::M + 64 + 31) / 32 + 3) & ~3u;
+    const RangeParams prm = *prm_g;
+    const uint32_t KW = prm.k_words;
+    uint32_t *wpat = smem;
+    uint32_t *PR = wpat + WP;
+    uint32_t *win = PR + ((KW + 3) & ~3u);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    build_wheel_pattern<WHEEL, NT>(wpat);
+    for (uint32_t i = threadIdx.x; i < KW; i += NT) PR[i] = t.PR[i];
+
+    const uint32_t rbits = prm.rec_bits < prm.tile_bits ? prm.rec_bits : prm.tile_bits;
+    const bool whole = prm.tile_bits >= prm.rec_bits;
+    const unsigned long long rmask = (1ull << prm.rec_bits) - 1ull;
+
+    for (;;) {
+        if (threadIdx.x == 0) s.tile = atomicAdd(&ctrl->tile_ctr, 1ull);
+        __syncthreads();
+        const unsigned long long tile = s.tile;
+        if (tile >= prm.ntiles) break;
+        const unsigned long long k0 = tile << prm.tile_bits;
+        const unsigned long long left = prm.n_total - k0;
+        const uint32_t cnt = left < (1ull << prm.tile_bits) ? (uint32_t)left : (1u << prm.tile_bits);
+        const unsigned long long n_lo = prm.n0 + 2ull * k0;
+        const WinGeom g = tile_geom(n_lo, cnt, 32u * KW);
+        build_window<WHEEL, NT>(win, wpat, g, t);
+
+        for (uint32_t ks = 0; ks < cnt; ks += (1u << rbits)) {
+            const uint32_t ke = (cnt - ks) < (1u << rbits) ? cnt : ks + (1u << rbits);
+            const unsigned long long kg = k0 + ks;
+            DevRec *rec = &recs[kg >> prm.rec_bits];
+            const unsigned long long kr0 = kg & rmask;
+            LaneAcc a;
+            a.reset();
+            if (threadIdx.x < HIST_BINS) s.hist[threadIdx.x] = 0u;
+            __syncthreads();
+            for (uint32_t g32 = (ks >> 5) + warp; (g32 << 5) < ke; g32 += NWARP) {
+                const uint32_t k = (g32 << 5) + lane;
+                const bool valid = k < ke;
+                const unsigned long long n = n_lo + 2ull * k;
+                uint32_t pm = fast_pmin(win, PR, KW, g32, valid && n != 4ull);
+                if (valid && n == 4ull) pm = 2u;
+                uint32_t pend = __ballot_sync(GB_FULL_MASK, valid && pm == 0u);
+                while (pend) {
+                    const int src = __ffs(pend) - 1;
+                    pend &= pend - 1;
+                    const unsigned long long ns = __shfl_sync(GB_FULL_MASK, n, src);
+                    unsigned long long ps = slow_pmin(ns, prm.p_slow_start, prm.slow_cap_log2, ctrl);
+                    if (ps >= PMIN_LIMIT) {
+                        if (lane == 0) atomicOr(&ctrl->flags, F_OVERFLOW);
+                        ps = PMIN_LIMIT - 1;
+                    }
+                    if (lane == src) {
+                        pm = (uint32_t)ps;
+                        if (!ps) a.ce = a.ce > ~ns ? a.ce : ~ns;
+                    }
+                }
+                if (valid && pm) a.add(pm, kr0 + (k - ks), prm.p_max, s.hist);
+            }
+            reduce_to_record<NT>(a, s, rec, ke - ks, whole, ctrl);
+        }
+    }
+}
+
+// Zero the control block and (when tiles share records) the records.
+__global__ void clear_kernel(const RangeParams *__restrict__ prm_g, DevRec *recs, Ctrl *ctrl,
+                             int clear_records)
+{
+    const RangeParams prm = *prm_g;
+    const unsigned long long tid = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+    if (tid == 0) {
+        ctrl->tile_ctr = 0; ctrl->ce_inv = 0; ctrl->slow_total = 0; ctrl->flags = 0;
+        ctrl->merge_done = 0; ctrl->work_ctr = 0;
+    }
+    if (!clear_records) return;
+    const unsigned long long words = prm.nrec * (sizeof(DevRec) / 16);
+    uint4 *p = reinterpret_cast<uint4 *>(recs);
+    const uint4 z = make_uint4(0, 0, 0, 0);
+    for (unsigned long long i = tid; i < words; i += (unsigned long long)gridDim.x * blockDim.x) p[i] = z;
+}
+
+// ---------------------------------------------------------------------------
+// merge: records -> gb_result
+// ---------------------------------------------------------------------------
+
+struct MergePart {
+    unsigned long long best_p, best_n, sum, wsum, n_count, n_slow, ce;
+    unsigned long long hist[HIST_BINS];
+};
+
+__device__ __forceinline__ bool better(unsigned long long p, unsigned long long n,
+                                       unsigned long long bp, unsigned long long bn)
+{
+    return p > bp || (p == bp && p != 0 && n < bn);
+}
+
+__global__ void __launch_bounds__(256)
+merge_kernel(const RangeParams *__restrict__ prm_g, const DevRec *__restrict__ recs, Ctrl *ctrl,
+             MergePart *parts, gb_result *out)
+{
+    __shared__ unsigned long long s_hist[HIST_BINS];
+    __shared__ unsigned long long s_bp[8], s_bn[8], s_sum[8], s_wsum[8], s_cnt[8], s_slow[8], s_ce[8];
+    __shared__ int s_last;
+    const RangeParams prm = *prm_g;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x < HIST_BINS) s_hist[threadIdx.x] = 0;
+    __syncthreads();
+    unsigned long long bp = 0, bn = ~0ull, sum = 0, wsum = 0, cnt = 0, slow = 0, ce = 0;
+    for (unsigned long long r = blockIdx.x * 256ull + threadIdx.x; r < prm.nrec;
+         r += (unsigned long long)gridDim.x * 256ull) {
+        const DevRec &R = recs[r];
+        const unsigned long long kfirst = r << prm.rec_bits;
+        const unsigned long long key = R.key;
+        if (key) {
+            unsigned long long p = key >> KEY_SHIFT;
+            unsigned long long n = prm.n0 + 2ull * (kfirst + (KEY_KMASK - (key & KEY_KMASK)));
+            if (better(p, n, bp, bn)) { bp = p; bn = n; }
+        }
+        sum += R.sum;
+        wsum += R.wsum + R.sum * kfirst;
+        cnt += R.n_count;
+        slow += R.n_slow;
+        ce = R.ce_inv > ce ? R.ce_inv : ce;
+        for (int b = 0; b < HIST_BINS; b++)
+            if (R.hist[b]) atomicAdd(&s_hist[b], R.hist[b]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long op = __shfl_xor_sync(GB_FULL_MASK, bp, o);
+        unsigned long long on = __shfl_xor_sync(GB_FULL_MASK, bn, o);
+        if (better(op, on, bp, bn)) { bp = op; bn = on; }
+        sum += __shfl_xor_sync(GB_FULL_MASK, sum, o);
+        wsum += __shfl_xor_sync(GB_FULL_MASK, wsum, o);
+        cnt += __shfl_xor_sync(GB_FULL_MASK, cnt, o);
+        slow += __shfl_xor_sync(GB_FULL_MASK, slow, o);
+        unsigned long long oc = __shfl_xor_sync(GB_FULL_MASK, ce, o);
+        ce = oc > ce ? oc : ce;
+    }
+    if (lane == 0) {
+        s_bp[warp] = bp; s_bn[warp] = bn; s_sum[warp] = sum; s_wsum[warp] = wsum;
+        s_cnt[warp] = cnt; s_slow[warp] = slow; s_ce[warp] = ce;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; w++) {
+            if (better(s_bp[w], s_bn[w], bp, bn)) { bp = s_bp[w]; bn = s_bn[w]; }
+            sum += s_sum[w]; wsum += s_wsum[w]; cnt += s_cnt[w]; slow += s_slow[w];
+            ce = s_ce[w] > ce ? s_ce[w] : ce;
+        }
+        MergePart &P = parts[blockIdx.x];
+        P.best_p = bp; P.best_n = bn; P.sum = sum; P.wsum = wsum; P.n_count = cnt;
+        P.n_slow = slow; P.ce = ce;
+    }
+    if (threadIdx.x < HIST_BINS) parts[blockIdx.x].hist[threadIdx.x] = s_hist[threadIdx.x];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(&ctrl->merge_done, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (threadIdx.x == 0) {
+        unsigned long long fp = 0, fn = ~0ull, fs = 0, fw = 0, fc = 0, fsl = 0, fce = 0;
+        for (unsigned int b = 0; b < gridDim.x; b++) {
+            const volatile MergePart &P = parts[b];
+            if (better(P.best_p, P.best_n, fp, fn)) { fp = P.best_p; fn = P.best_n; }
+            fs += P.sum; fw += P.wsum; fc += P.n_count; fsl += P.n_slow;
+            fce = P.ce > fce ? P.ce : fce;
+        }
+        out->n_first = prm.n_total ? prm.n0 : 0;
+        out->n_count = fc;
+        out->max_pmin = fp;
+        out->argmax_n = fp ? fn : 0;
+        out->sum_pmin = fs;
+        out->wsum_pmin = fw;
+        out->n_slow = fsl;
+        const unsigned long long ci = fce > ctrl->ce_inv ? fce : ctrl->ce_inv;
+        const unsigned long long cen = ci ? ~ci : 0ull;
+        out->counterexample_n = cen;
+        const unsigned int f = ctrl->flags;
+        int st = GB_OK;
+        if (f & F_INTERNAL) st = GB_EINTERNAL;
+        else if (f & F_SLOWCAP) st = GB_ESLOWPATH_LIMIT;
+        else if (f & F_OVERFLOW) st = GB_EOVERFLOW;
+        else if ((f & F_COUNTEREX) || cen) st = GB_COUNTEREXAMPLE;
+        out->status = st;
+        out->reserved = 0;
+    }
+    if (threadIdx.x < 64) {
+        unsigned long long h = 0;
+        if (threadIdx.x < HIST_BINS)
+            for (unsigned int b = 0; b < gridDim.x; b++)
+                h += ((const volatile MergePart &)parts[b]).hist[threadIdx.x];
+        out->hist[threadIdx.x] = h;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// plain per-segment form
+// ---------------------------------------------------------------------------
+
+// Window slice [z0, z0 + Z) of a window described by (half_abs, neg, j_end).
+__device__ __forceinline__ WinGeom slice_geom(unsigned long long half_abs, bool neg, uint32_t j_end,
+                                              uint32_t z0, uint32_t Z)
+{
+    unsigned long long h2;
+    bool n2;
+    if (neg) {
+        n2 = half_abs > z0;
+        h2 = n2 ? half_abs - z0 : z0 - half_abs;
+    } else {
+        n2 = false;
+        h2 = half_abs + z0;
+    }
+    uint32_t je = j_end - z0 < Z ? j_end - z0 : Z;
+    return make_geom(h2, n2, je);
+}
+
+// One CTA builds slice blockIdx.x of the window in shared memory and flushes
+// it to the global bitset with 16-byte stores.
+template <int WHEEL, int NT>
+__global__ void __launch_bounds__(NT, 1)
+slice_sieve_kernel(unsigned long long half_abs, int neg, uint32_t j_end, uint32_t Z, Tables t,
+                   uint32_t *__restrict__ gwin, uint32_t gwords)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    constexpr uint32_t WP = ((WheelM<WHEEL>::M + 64 + 31) / 32 + 3) & ~3u;
+    uint32_t *wpat = smem;
+    uint32_t *win = smem + WP;
+    build_wheel_pattern<WHEEL, NT>(wpat);
+    __syncthreads();
+    const uint32_t z0 = blockIdx.x * Z;
+    const WinGeom g = slice_geom(half_abs, neg != 0, j_end, z0, Z);
+    build_window<WHEEL, NT>(win, wpat, g, t);
+    // words of this slice: Z/32, except the last slice which also writes its
+    // trailing zero word(s); never write a word owned by the next slice.
+    const uint32_t w0 = z0 >> 5;
+    uint32_t nw = (z0 + Z >= j_end) ? g.nfill : (Z >> 5);
+    if (w0 + nw > gwords) nw = gwords - w0;
+    const uint32_t n4 = nw >> 2;
+    uint4 *dst = reinterpret_cast<uint4 *>(gwin + w0);
+    const uint4 *src = reinterpret_cast<const uint4 *>(win);
+    for (uint32_t i = threadIdx.x; i < n4; i += NT) dst[i] = src[i];
+    for (uint32_t i = 4 * n4 + threadIdx.x; i < nw; i += NT) gwin[w0 + i] = win[i];
+}
+
+// p_min for every n of a plain segment, read from the global window bitset.
+__global__ void __launch_bounds__(256)
+plain_search_kernel(const RangeParams *__restrict__ prm_g, const uint32_t *__restrict__ gwin,
+                    const uint32_t *__restrict__ PR, unsigned long long n_lo, uint32_t cnt,
+                    uint32_t *__restrict__ pm_out, Ctrl *ctrl)
+{
+    const RangeParams prm = *prm_g;
+    const int lane = threadIdx.x & 31;
+    const uint32_t nchunks = (cnt + 31) >> 5;
+    for (uint32_t g32 = (blockIdx.x * 256u + threadIdx.x) >> 5; g32 < nchunks;
+         g32 += (gridDim.x * 256u) >> 5) {
+        const uint32_t k = (g32 << 5) + lane;
+        const bool valid = k < cnt;
+        const unsigned long long n = n_lo + 2ull * k;
+        uint32_t pm = fast_pmin(gwin, PR, prm.k_words, g32, valid && n != 4ull);
+        if (valid && n == 4ull) pm = 2u;
+        uint32_t pend = __ballot_sync(GB_FULL_MASK, valid && pm == 0u);
+        while (pend) {
+            const int src = __ffs(pend) - 1;
+            pend &= pend - 1;
+            const unsigned long long ns = __shfl_sync(GB_FULL_MASK, n, src);
+            unsigned long long ps = slow_pmin(ns, prm.p_slow_start, prm.slow_cap_log2, ctrl);
+            if (ps >= PMIN_LIMIT) {
+                if (lane == 0) atomicOr(&ctrl->flags, F_OVERFLOW);
+                ps = PMIN_LIMIT - 1;
+            }
+            if (lane == src) pm = (uint32_t)ps;
+        }
+        if (valid) pm_out[k] = pm;
+    }
+}
+
+// Reduce chunks of the p_min array into (zeroed) records with atomics.
+template <int NT>
+__global__ void __launch_bounds__(NT)
+plain_reduce_kernel(const RangeParams *__restrict__ prm_g, const uint32_t *__restrict__ pm,
+                    unsigned long long k_seg0, unsigned long long n_lo, uint32_t cnt,
+                    uint32_t chunk, DevRec *recs, Ctrl *ctrl)
+{
+    __shared__ RedScratch s;
+    const RangeParams prm = *prm_g;
+    const uint32_t rbits = prm.rec_bits;
+    const unsigned long long rmask = (1ull << rbits) - 1ull;
+    // chunk boundaries never straddle a record: chunk divides 2^rec_bits or vice versa
+    const uint32_t ks = blockIdx.x * chunk;
+    if (ks >= cnt) return;
+    const uint32_t ke = cnt - ks < chunk ? cnt : ks + chunk;
+    const unsigned long long kg = k_seg0 + ks;
+    DevRec *rec = &recs[kg >> rbits];
+    const unsigned long long kr0 = kg & rmask;
+    LaneAcc a;
+    a.reset();
+    if (threadIdx.x < HIST_BINS) s.hist[threadIdx.x] = 0u;
+    __syncthreads();
+    for (uint32_t k = ks + threadIdx.x; k < ke; k += NT) {
+        const uint32_t p = pm[k];
+        if (p) a.add(p, kr0 + (k - ks), prm.p_max, s.hist);
+        else a.ce = a.ce > ~(n_lo + 2ull * k) ? a.ce : ~(n_lo + 2ull * k);
+    }
+    reduce_to_record<NT>(a, s, rec, ke - ks, false, ctrl);
+}
+
+// ---------------------------------------------------------------------------
+// base-prime table: compaction of a sieved bitset of odd numbers
+// ---------------------------------------------------------------------------
+
+constexpr uint32_t TBL_WORDS_PER_BLOCK = 8192;
+
+__global__ void table_count_kernel(const uint32_t *__restrict__ bits, uint32_t nwords,
+                                   uint32_t *__restrict__ block_counts)
+{
+    __shared__ uint32_t s_c;
+    if (threadIdx.x == 0) s_c = 0;
+    __syncthreads();
+    const uint32_t w0 = blockIdx.x * TBL_WORDS_PER_BLOCK;
+    uint32_t c = 0;
+    for (uint32_t i = threadIdx.x; i < TBL_WORDS_PER_BLOCK && w0 + i < nwords; i += blockDim.x)
+        c += __popc(bits[w0 + i]);
+    c = __reduce_add_sync(GB_FULL_MASK, c);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&s_c, c);
+    __syncthreads();
+    if (threadIdx.x == 0) block_counts[blockIdx.x] = s_c;
+}
+
+// Each block re-reads its words; thread i owns 8 consecutive words, a block
+// scan of the per-thread counts gives every prime its output slot.
+__global__ void __launch_bounds__(1024)
+table_scatter_kernel(const uint32_t *__restrict__ bits, uint32_t nwords,
+                     const unsigned long long *__restrict__ block_offsets, unsigned long long limit,
+                     uint32_t *__restrict__ primes, unsigned long long *__restrict__ recip)
+{
+    __shared__ uint32_t s_warp[32];
+    const uint32_t w0 = blockIdx.x * TBL_WORDS_PER_BLOCK + threadIdx.x * 8u;
+    uint32_t wd[8];
+    uint32_t c = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        wd[i] = (w0 + i < nwords) ? bits[w0 + i] : 0u;
+        c += __popc(wd[i]);
+    }
+    // block exclusive scan of c
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(GB_FULL_MASK, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t v = s_warp[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(GB_FULL_MASK, v, o);
+            if (lane >= o) v += y;
+        }
+        s_warp[lane] = v;
+    }
+    __syncthreads();
+    unsigned long long pos = block_offsets[blockIdx.x] + (x - c) + (warp ? s_warp[warp - 1] : 0u);
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        uint32_t w = wd[i];
+        while (w) {
+            const int b = __ffs(w) - 1;
+            w &= w - 1;
+            const unsigned long long q = 2ull * (32ull * (w0 + i) + b) + 1ull;
+            if (q <= limit) {
+                primes[pos] = (uint32_t)q;
+                recip[pos] = 0xFFFFFFFFFFFFFFFFull / q;
+            }
+            pos++;
+        }
+    }
+}
+
+__global__ void exclusive_scan_small_kernel(const uint32_t *__restrict__ in, uint32_t n,
+                                            unsigned long long *__restrict__ out)
+{
+    // one thread: n is at most a few tens of thousands
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        unsigned long long acc = 0;
+        for (uint32_t i = 0; i < n; i++) { out[i] = acc; acc += in[i]; }
+        out[n] = acc;
+    }
+}
+
+__global__ void set_params_kernel(RangeParams *dst, RangeParams p)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *dst = p;
+}
+
+// ---------------------------------------------------------------------------
+// host-side launch wrappers
+// ---------------------------------------------------------------------------
+
+cudaError_t launch_set_params(cudaStream_t st, RangeParams *dst, const RangeParams &p)
+{
+    set_params_kernel<<<1, 32, 0, st>>>(dst, p);
+    return cudaGetLastError();
+}
+
+template <int WHEEL, int NT>
+static const void *persistent_ptr() { return (const void *)persistent_kernel<WHEEL, NT>; }
+template <int WHEEL, int NT>
+static const void *slice_ptr() { return (const void *)slice_sieve_kernel<WHEEL, NT>; }
+
+const void *persistent_kernel_ptr(int wheel, int nt)
+{
+    if (wheel == 13) {
+        if (nt == 256) return persistent_ptr<13, 256>();
+        if (nt == 512) return persistent_ptr<13, 512>();
+        if (nt == 1024) return persistent_ptr<13, 1024>();
+    } else if (wheel == 7) {
+        if (nt == 256) return persistent_ptr<7, 256>();
+        if (nt == 512) return persistent_ptr<7, 512>();
+        if (nt == 1024) return persistent_ptr<7, 1024>();
+    }
+    return nullptr;
+}
+
+const void *slice_kernel_ptr(int wheel, int nt)
+{
+    if (wheel == 13) {
+        if (nt == 256) return slice_ptr<13, 256>();
+        if (nt == 512) return slice_ptr<13, 512>();
+        if (nt == 1024) return slice_ptr<13, 1024>();
+    } else if (wheel == 7) {
+        if (nt == 256) return slice_ptr<7, 256>();
+        if (nt == 512) return slice_ptr<7, 512>();
+        if (nt == 1024) return slice_ptr<7, 1024>();
+    }
+    return nullptr;
+}
+
+uint32_t wheel_pattern_words(int wheel)
+{
+    return wheel == 13 ? (((WheelM<13>::M + 64 + 31) / 32 + 3) & ~3u)
+                       : (((WheelM<7>::M + 64 + 31) / 32 + 3) & ~3u);
+}
+
+cudaError_t launch_persistent(int wheel, int nt, int grid, size_t smem, cudaStream_t st,
+                              const RangeParams *prm, const Tables &t, DevRec *recs, Ctrl *ctrl)
+{
+    const void *fn = persistent_kernel_ptr(wheel, nt);
+    if (!fn) return cudaErrorInvalidValue;
+    Tables tt = t;
+    void *args[] = {(void *)&prm, (void *)&tt, (void *)&recs, (void *)&ctrl};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(nt), args, smem, st);
+}
+
+cudaError_t launch_clear(cudaStream_t st, const RangeParams *prm, DevRec *recs, Ctrl *ctrl,
+                         int clear_records, int grid)
+{
+    clear_kernel<<<grid, 256, 0, st>>>(prm, recs, ctrl, clear_records);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_merge(cudaStream_t st, int grid, const RangeParams *prm, const DevRec *recs,
+                         Ctrl *ctrl, void *parts, gb_result *out)
+{
+    merge_kernel<<<grid, 256, 0, st>>>(prm, recs, ctrl, (MergePart *)parts, out);
+    return cudaGetLastError();
+}
+
+size_t merge_part_bytes() { return sizeof(MergePart); }
+
+cudaError_t launch_slice_sieve(int wheel, int nt, int grid, size_t smem, cudaStream_t st,
+                               unsigned long long half_abs, int neg, uint32_t j_end, uint32_t Z,
+                               const Tables &t, uint32_t *gwin, uint32_t gwords)
+{
+    const void *fn = slice_kernel_ptr(wheel, nt);
+    if (!fn) return cudaErrorInvalidValue;
+    Tables tt = t;
+    void *args[] = {(void *)&half_abs, (void *)&neg, (void *)&j_end, (void *)&Z, (void *)&tt,
+                    (void *)&gwin, (void *)&gwords};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(nt), args, smem, st);
+}
+
+cudaError_t launch_plain_search(cudaStream_t st, int grid, const RangeParams *prm,
+                                const uint32_t *gwin, const uint32_t *PR, unsigned long long n_lo,
+                                uint32_t cnt, uint32_t *pm, Ctrl *ctrl)
+{
+    plain_search_kernel<<<grid, 256, 0, st>>>(prm, gwin, PR, n_lo, cnt, pm, ctrl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plain_reduce(cudaStream_t st, const RangeParams *prm, const uint32_t *pm,
+                                unsigned long long k_seg0, unsigned long long n_lo, uint32_t cnt,
+                                uint32_t chunk, DevRec *recs, Ctrl *ctrl)
+{
+    const uint32_t grid = (cnt + chunk - 1) / chunk;
+    plain_reduce_kernel<256><<<grid, 256, 0, st>>>(prm, pm, k_seg0, n_lo, cnt, chunk, recs, ctrl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_table_compact(cudaStream_t st, const uint32_t *bits, uint32_t nwords,
+                                 uint32_t *block_counts, unsigned long long *block_offsets,
+                                 unsigned long long limit, uint32_t *primes,
+                                 unsigned long long *recip, int count_only)
+{
+    const uint32_t nb = (nwords + TBL_WORDS_PER_BLOCK - 1) / TBL_WORDS_PER_BLOCK;
+    if (count_only) {
+        table_count_kernel<<<nb, 256, 0, st>>>(bits, nwords, block_counts);
+        exclusive_scan_small_kernel<<<1, 32, 0, st>>>(block_counts, nb, block_offsets);
+    } else {
+        table_scatter_kernel<<<nb, 1024, 0, st>>>(bits, nwords, block_offsets, limit, primes, recip);
+    }
+    return cudaGetLastError();
+}
+
+uint32_t table_blocks(uint32_t nwords) { return (nwords + TBL_WORDS_PER_BLOCK - 1) / TBL_WORDS_PER_BLOCK; }
+
+}  // namespace gbk

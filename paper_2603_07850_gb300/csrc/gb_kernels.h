@@ -1,0 +1,41 @@
+// gb_kernels.h -- host-callable launch wrappers for the kernels in gb_kernels.cu.
+#pragma once
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime.h>
+
+#include "gb_types.h"
+
+namespace gbk {
+
+const void *persistent_kernel_ptr(int wheel, int nt);
+const void *slice_kernel_ptr(int wheel, int nt);
+uint32_t wheel_pattern_words(int wheel);
+size_t merge_part_bytes();
+uint32_t table_blocks(uint32_t nwords);
+
+cudaError_t launch_persistent(int wheel, int nt, int grid, size_t smem, cudaStream_t st,
+                              const RangeParams *prm, const Tables &t, DevRec *recs, Ctrl *ctrl);
+cudaError_t launch_clear(cudaStream_t st, const RangeParams *prm, DevRec *recs, Ctrl *ctrl,
+                         int clear_records, int grid);
+cudaError_t launch_merge(cudaStream_t st, int grid, const RangeParams *prm, const DevRec *recs,
+                         Ctrl *ctrl, void *parts, gb_result *out);
+cudaError_t launch_slice_sieve(int wheel, int nt, int grid, size_t smem, cudaStream_t st,
+                               unsigned long long half_abs, int neg, uint32_t j_end, uint32_t Z,
+                               const Tables &t, uint32_t *gwin, uint32_t gwords);
+cudaError_t launch_plain_search(cudaStream_t st, int grid, const RangeParams *prm,
+                                const uint32_t *gwin, const uint32_t *PR, unsigned long long n_lo,
+                                uint32_t cnt, uint32_t *pm, Ctrl *ctrl);
+cudaError_t launch_plain_reduce(cudaStream_t st, const RangeParams *prm, const uint32_t *pm,
+                                unsigned long long k_seg0, unsigned long long n_lo, uint32_t cnt,
+                                uint32_t chunk, DevRec *recs, Ctrl *ctrl);
+cudaError_t launch_table_compact(cudaStream_t st, const uint32_t *bits, uint32_t nwords,
+                                 uint32_t *block_counts, unsigned long long *block_offsets,
+                                 unsigned long long limit, uint32_t *primes,
+                                 unsigned long long *recip, int count_only);
+
+}  // namespace gbk
+
+namespace gbk {
+cudaError_t launch_set_params(cudaStream_t st, RangeParams *dst, const RangeParams &p);
+}

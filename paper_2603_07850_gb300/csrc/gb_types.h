@@ -1,0 +1,68 @@
+// gb_types.h -- layouts shared by the kernels and the host side of the library.
+#pragma once
+#include <stdint.h>
+#include <cuda_runtime.h>
+
+#include "../../include/goldbach_gb300.h"
+
+namespace gbk {
+
+// Ctrl::flags bits
+enum : uint32_t { F_COUNTEREX = 1u, F_SLOWCAP = 2u, F_OVERFLOW = 4u, F_INTERNAL = 8u };
+
+// Record key: (max_pmin << 40) | (2^40 - 1 - k_argmax), so one 64-bit
+// atomicMax keeps the largest p_min and, on ties, the smallest n.
+constexpr int KEY_SHIFT = 40;
+constexpr uint64_t KEY_KMASK = (1ull << KEY_SHIFT) - 1;
+constexpr uint32_t PMIN_LIMIT = 1u << 24;   // p_min must stay below this for the key
+constexpr int HIST_BINS = 32;
+
+struct __align__(16) DevRec {         // 304 bytes
+    unsigned long long key;            // 0 = no n folded yet
+    unsigned long long sum;
+    unsigned long long wsum;
+    unsigned long long n_count;
+    unsigned long long n_slow;
+    unsigned long long ce_inv;         // ~n of the smallest counterexample, 0 = none
+    unsigned long long hist[HIST_BINS];
+};
+
+struct __align__(16) Ctrl {
+    unsigned long long tile_ctr;       // next tile to claim (device atomic pool)
+    unsigned long long ce_inv;         // ~n of the smallest counterexample
+    unsigned long long slow_total;
+    unsigned int flags;
+    unsigned int merge_done;
+    unsigned long long work_ctr;       // serving: next work item
+    unsigned long long pad[3];
+};
+
+// Everything a launch needs to know about one call, kept in device memory so a
+// captured graph can be replayed with new ranges.
+struct __align__(16) RangeParams {
+    unsigned long long n0;             // first even n of the range
+    unsigned long long n_total;        // number of even n
+    unsigned long long ntiles;
+    unsigned long long nrec;
+    unsigned long long p_slow_start;   // smallest odd p > P_max
+    unsigned int tile_bits;            // log2 even n per tile
+    unsigned int rec_bits;             // log2 even n per record
+    unsigned int k_words;              // candidate words (K_bits = 32 k_words)
+    unsigned int p_max;
+    unsigned int slow_cap_log2;
+    unsigned int pad0;
+};
+
+// Read-only device tables shared by every kernel.
+struct Tables {
+    const uint32_t *primes;            // odd primes ascending, primes[0] = 3
+    const unsigned long long *recip;   // floor((2^64 - 1) / p)
+    const uint32_t *PR;                // bit-reversed candidate words
+    uint32_t nprimes;
+    uint32_t iA0;                      // first prime index that is marked (above the patterns)
+    uint32_t iB0;                      // first prime index marked lane-per-prime
+    uint32_t pat_lo, pat_hi;           // in-register pattern primes PAT[pat_lo .. pat_hi)
+    uint32_t k_words;
+};
+
+}  // namespace gbk
