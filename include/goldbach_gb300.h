@@ -196,6 +196,40 @@ int gb_verify_range_plain(uint64_t lo, uint64_t hi, gb_seg_record *buf, size_t c
  */
 int gb_verify_range_async(uint64_t lo, uint64_t hi, gb_result *dev_out, void *stream);
 
+/*
+ * gb_verify_range_noalloc -- gb_verify_range for callers that cannot
+ * allocate device memory.  (This entry point has no counterpart in the
+ * paper; it is a deployment convenience.)
+ *
+ * Some programs must not call cudaMalloc where they verify a range: their
+ * GPU memory may be wholly reserved by another allocator (a framework's
+ * caching pool, where a stray allocation fails or fragments the pool), or
+ * they run a latency-critical loop in which cudaMalloc/cudaFree would stall
+ * on an implicit device synchronisation.  gb_init allocates, so such callers
+ * use this function instead; it needs no gb_init and allocates nothing.
+ *
+ * All working memory (base primes <= 2^20, candidate words, parameters,
+ * control block, records, merge partials) is one static device array of
+ * about 3.7 MB that every GPU loading this library holds until the process
+ * exits.  Limits, rejected with GB_EINVAL and a message in gb_last_error():
+ *   2 <= p_max <= 2^16;  5 <= seg_bits <= 40;  every n < 2^40;
+ *   at most 8192 records of 2^seg_bits even n (pick seg_bits accordingly).
+ *
+ *   dev_out : DEVICE pointer to a gb_result, written when the stream gets
+ *             there (status in dev_out->status).
+ *   stream  : cudaStream_t to enqueue on (NULL = the default stream).
+ *
+ * The first call on each device does a one-time set-up with that device
+ * current: it looks up the scratch address, builds the base-prime table in
+ * it and synchronises the stream.  Make that first call before any stream
+ * capture.  Later calls only enqueue work.  Every call reuses the same
+ * scratch (and clears what must start at zero), so calls that overlap on the
+ * GPU race: serialise them, e.g. on one stream.
+ * Returns GB_OK once enqueued, GB_EINVAL, GB_ECUDA or GB_EINTERNAL.
+ */
+int gb_verify_range_noalloc(uint64_t lo, uint64_t hi, uint32_t p_max, uint32_t seg_bits,
+                            gb_result *dev_out, void *stream);
+
 /* ---- serving (continuous batching) ------------------------------------------ */
 
 /*

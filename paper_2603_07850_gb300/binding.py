@@ -95,6 +95,8 @@ def load(path: str = LIB_PATH):
         "gb_verify_range_segments": ([U64, U64, ctypes.c_void_p, sz, P(sz), P(GbResult)], ctypes.c_int),
         "gb_verify_range_plain": ([U64, U64, ctypes.c_void_p, sz, P(sz), P(GbResult)], ctypes.c_int),
         "gb_verify_range_async": ([U64, U64, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+        "gb_verify_range_noalloc": ([U64, U64, u32, u32, ctypes.c_void_p, ctypes.c_void_p],
+                                    ctypes.c_int),
         "gb_submit": ([U64, U64, P(U64)], ctypes.c_int),
         "gb_poll": ([U64, P(GbResult), i32], ctypes.c_int),
         "gb_stats": ([P(GbStats)], ctypes.c_int),
@@ -168,6 +170,15 @@ def gb_verify_range_async(lo: int, hi: int, dev_out_ptr: int, stream_ptr: int = 
     _check("gb_verify_range_async",
            load().gb_verify_range_async(lo, hi, ctypes.c_void_p(dev_out_ptr),
                                         ctypes.c_void_p(stream_ptr or None)))
+
+
+def gb_verify_range_noalloc(lo: int, hi: int, p_max: int, seg_bits: int, dev_out_ptr: int,
+                            stream_ptr: int = 0) -> None:
+    """Allocation-free verification into a caller-owned device gb_result
+    (for callers that cannot call cudaMalloc; see the C header)."""
+    _check("gb_verify_range_noalloc",
+           load().gb_verify_range_noalloc(lo, hi, p_max, seg_bits, ctypes.c_void_p(dev_out_ptr),
+                                          ctypes.c_void_p(stream_ptr or None)))
 
 
 def gb_submit(lo: int, hi: int) -> int:
