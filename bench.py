@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n-top", type=int, default=N_TOP)
     ap.add_argument("--no-plain", action="store_true")
-    ap.add_argument("--cpu-records", type=int, default=24)
+    ap.add_argument("--cpu-records", type=int, default=600)
     return ap.parse_args()
 
 

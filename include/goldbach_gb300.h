@@ -140,6 +140,12 @@ int gb_init(uint32_t p_max, uint32_t seg_bits);
  *   "tier_b_min"    smallest prime crossed off lane-per-prime (default 4096)
  *   "plain_slice_bits" log2 window bits per CTA in the plain sieve kernel (default 18)
  *   "time_kernel"   1 = time the persistent kernel with CUDA events (default 0)
+ *   "search_pmax"   bound of the in-window candidate search, 0 = P_max (default 0);
+ *                   n with p_min above it take the slow path, but n_slow and
+ *                   every other output still refer to P_max
+ *   "bucket_min"    smallest base prime handled by the bucket pre-pass,
+ *                   0 = the window span (default), else >= 64
+ *   "bucket_chunk_tiles" tiles per bucket pre-pass chunk, 1..8192 (default 2048)
  * Returns GB_OK or GB_EINVAL (unknown key or value out of range).
  */
 int gb_set_option(const char *key, int64_t value);

@@ -51,6 +51,9 @@ struct Options {
     int64_t timeout_ms = 600000;
     int64_t serve_batch_tiles = 4096;
     int64_t time_kernel = 0;       // record CUDA events around the persistent kernel
+    int64_t bucket_min = 0;        // smallest bucketed prime; 0 = the window span S + K
+    int64_t bucket_chunk_tiles = 2048;
+    int64_t search_pmax = 0;       // window search bound; 0 = P_max
 };
 
 struct GraphKey {
@@ -98,10 +101,18 @@ struct Ctx {
     gb_stats_t stats{};
     size_t device_bytes = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // persistent-kernel timing (time_kernel)
+    // bucket pre-pass buffers
+    unsigned int *d_bk_counts = nullptr, *d_bk_cursor = nullptr;
+    unsigned long long *d_bk_off = nullptr;
+    size_t bk_tiles_cap = 0;
+    uint32_t *d_bk_ent = nullptr;
+    size_t bk_ent_cap = 0;
+    std::map<uint64_t, uint32_t> odd_primes_below;  // cache: bound -> #odd primes below it
     bool ev_pending = false;
 };
 
 Ctx g;
+uint32_t search_pmax();
 std::recursive_mutex g_mu;
 std::mutex g_err_mu;
 std::string g_err = "";
@@ -325,12 +336,17 @@ void fill_params(const CallPlan &cp, uint32_t tile_bits, RangeParams &p)
     p.n_total = cp.n_total;
     p.ntiles = cp.ntiles;
     p.nrec = cp.nrec;
-    p.p_slow_start = (g.p_max + 1ull) | 1ull;
+    p.p_slow_start = (search_pmax() + 1ull) | 1ull;
     p.tile_bits = tile_bits;
     p.rec_bits = g.seg_bits;
     p.k_words = g.k_words;
     p.p_max = g.p_max;
     p.slow_cap_log2 = (uint32_t)g.opt.slow_cap;
+    p.bk_prime0 = 0xffffffffu;
+    p.tile0 = 0;
+    p.tile_end = cp.ntiles;
+    p.bk_off = nullptr;
+    p.bk_ent = nullptr;
 }
 
 void empty_result(gb_result *out)
@@ -391,6 +407,106 @@ int enqueue_persistent(cudaStream_t st, const CallPlan &cp, gb_result *dev_out, 
     return GB_OK;
 }
 
+// Smallest prime handled by the bucket pre-pass for this configuration.
+uint64_t bucket_bound()
+{
+    if (g.opt.bucket_min > 0) return (uint64_t)g.opt.bucket_min;
+    return (1ull << g.opt.tile_bits) + 32ull * g.k_words;
+}
+
+uint32_t count_odd_primes_below(uint64_t x)
+{
+    auto it = g.odd_primes_below.find(x);
+    if (it != g.odd_primes_below.end()) return it->second;
+    uint32_t c;
+    if (x <= (1u << 16)) {
+        c = (uint32_t)(std::lower_bound(g.h_small.begin(), g.h_small.end(), (uint32_t)x) - g.h_small.begin());
+    } else {
+        std::vector<uint32_t> v = host_odd_primes((uint32_t)std::min<uint64_t>(x, 0xFFFFFFFFull));
+        c = (uint32_t)(std::lower_bound(v.begin(), v.end(), (uint32_t)std::min<uint64_t>(x, 0xFFFFFFFFull)) -
+                       v.begin());
+    }
+    g.odd_primes_below[x] = c;
+    return c;
+}
+
+bool needs_buckets(const CallPlan &cp)
+{
+    const uint64_t n_last = cp.n0 + 2 * (cp.n_total - 1);
+    return isqrt_host(n_last) >= bucket_bound();
+}
+
+// Persistent pipeline with the large primes bucketed: tiles are processed in
+// chunks; per chunk the pre-pass counts, scans and fills the buckets, then
+// the persistent kernel sieves the chunk's tiles.
+int run_persistent_buckets(const CallPlan &cp, int grid, size_t smem, int mg, gb_result *dev_out,
+                           cudaStream_t st, bool sync_result)
+{
+    int rc;
+    const uint64_t B = bucket_bound();
+    if (B > (1ull << 22)) { set_error("bucket_min above 2^22 is not supported"); return GB_EINVAL; }
+    const uint32_t i0 = count_odd_primes_below(B);
+    const uint64_t CT = (uint64_t)g.opt.bucket_chunk_tiles;
+    if (g.bk_tiles_cap < CT + 1) {
+        dev_free(&g.d_bk_counts, 4 * g.bk_tiles_cap);
+        dev_free(&g.d_bk_cursor, 4 * g.bk_tiles_cap);
+        dev_free(&g.d_bk_off, 8 * g.bk_tiles_cap);
+        g.bk_tiles_cap = 0;
+        if ((rc = dev_alloc(&g.d_bk_counts, 4 * (CT + 1)))) return rc;
+        if ((rc = dev_alloc(&g.d_bk_cursor, 4 * (CT + 1)))) return rc;
+        if ((rc = dev_alloc(&g.d_bk_off, 8 * (CT + 1)))) return rc;
+        g.bk_tiles_cap = CT + 1;
+    }
+    RangeParams p;
+    fill_params(cp, (uint32_t)g.opt.tile_bits, p);
+    p.bk_prime0 = i0;
+    Tables t = make_tables();
+    const int clear_records = g.opt.tile_bits < g.seg_bits ? 1 : 0;
+    CK(launch_set_params(st, g.d_params, p));
+    CK(launch_clear(st, g.d_params, g.d_recs, g.d_ctrl, clear_records, clear_records ? 4 * g.sms : 1));
+    uint64_t launches = 2;
+    for (uint64_t t0 = 0; t0 < cp.ntiles; t0 += CT) {
+        const uint32_t nt = (uint32_t)std::min<uint64_t>(CT, cp.ntiles - t0);
+        CK(cudaMemsetAsync(g.d_bk_counts, 0, 4ull * nt, st));
+        CK(launch_bucket_prepass(st, 4 * g.sms, g.d_params, t, i0, t0, nt, g.d_bk_counts, g.d_bk_off,
+                                 g.d_bk_cursor, nullptr, 0));
+        unsigned long long total = 0;
+        CK(cudaMemcpyAsync(&total, g.d_bk_off + nt, 8, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (total >= (1ull << 32)) { set_error("bucket chunk too large: lower bucket_chunk_tiles"); return GB_ENOMEM; }
+        if (total > g.bk_ent_cap) {
+            dev_free(&g.d_bk_ent, 4 * g.bk_ent_cap);
+            g.bk_ent_cap = 0;
+            size_t cap = (size_t)(total + total / 8 + 1024);
+            if ((rc = dev_alloc(&g.d_bk_ent, 4 * cap))) return rc;
+            g.bk_ent_cap = cap;
+        }
+        CK(launch_bucket_prepass(st, 4 * g.sms, g.d_params, t, i0, t0, nt, g.d_bk_counts, g.d_bk_off,
+                                 g.d_bk_cursor, g.d_bk_ent, 1));
+        p.tile0 = t0;
+        p.tile_end = t0 + nt;
+        p.bk_off = g.d_bk_off;
+        p.bk_ent = g.d_bk_ent;
+        CK(launch_set_params(st, g.d_params, p));
+        CK(cudaMemsetAsync(&g.d_ctrl->tile_ctr, 0, 8, st));
+        CK(launch_persistent((int)g.opt.wheel, (int)g.opt.threads, grid, smem, st, g.d_params, t, g.d_recs,
+                             g.d_ctrl));
+        launches += 5;
+    }
+    p.tile0 = 0;
+    p.tile_end = cp.ntiles;
+    CK(launch_set_params(st, g.d_params, p));
+    CK(launch_merge(st, mg, g.d_params, g.d_recs, g.d_ctrl, g.d_parts, dev_out));
+    launches += 2;
+    if (sync_result) {
+        CK(cudaMemcpyAsync(g.h_result, dev_out, sizeof(gb_result), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    g.stats.kernel_launches += launches;
+    g.stats.tiles += cp.ntiles;
+    return GB_OK;
+}
+
 int run_persistent(uint64_t lo, uint64_t hi, CallPlan &cp)
 {
     int rc = plan_range(lo, hi, cp);
@@ -404,6 +520,7 @@ int run_persistent(uint64_t lo, uint64_t hi, CallPlan &cp)
     int grid = 0;
     if ((rc = occupancy_grid(fn, nt, smem, &grid))) return rc;
     const int mg = merge_grid_for(cp.nrec);
+    if (needs_buckets(cp)) return run_persistent_buckets(cp, grid, smem, mg, g.d_result, g.stream, true);
     fill_params(cp, tile_bits, *g.h_params);
     const int clear_records = g.opt.tile_bits < g.seg_bits ? 1 : 0;
     if (g.opt.use_graph) {
@@ -483,6 +600,11 @@ int run_plain(uint64_t lo, uint64_t hi, CallPlan &cp)
     int rc = plan_range(lo, hi, cp);
     if (rc) return rc;
     if (!cp.n_total) return GB_OK;
+    if (needs_buckets(cp)) {
+        set_error("the plain form has no bucket pass: its ranges must keep sqrt(n) below the "
+                  "bucket bound (%llu)", (unsigned long long)bucket_bound());
+        return GB_EINVAL;
+    }
     if ((rc = prepare_common(cp))) return rc;
     const uint32_t sbits = (uint32_t)g.opt.plain_seg_bits;
     const uint64_t S = 1ull << sbits;
@@ -556,6 +678,10 @@ void release_all()
     dev_free(&g.d_result, sizeof(gb_result));
     dev_free(&g.d_gwin, 4 * g.gwin_words);
     dev_free(&g.d_pm, 4 * g.pm_cap);
+    dev_free(&g.d_bk_counts, 4 * g.bk_tiles_cap);
+    dev_free(&g.d_bk_cursor, 4 * g.bk_tiles_cap);
+    dev_free(&g.d_bk_off, 8 * g.bk_tiles_cap);
+    dev_free(&g.d_bk_ent, 4 * g.bk_ent_cap);
     if (g.h_params) cudaFreeHost(g.h_params);
     if (g.h_result) cudaFreeHost(g.h_result);
     if (g.h_flags) cudaFreeHost(g.h_flags);
@@ -565,6 +691,39 @@ void release_all()
     Options keep = g.opt;
     g = Ctx{};
     g.opt = keep;
+}
+
+// The window search bound: the caller's P_max unless "search_pmax" sets a
+// different one.  It only decides which n take the slow path; n_slow still
+// counts p_min > P_max, so the records do not depend on it.
+uint32_t search_pmax()
+{
+    return g.opt.search_pmax > 0 ? (uint32_t)g.opt.search_pmax : g.p_max;
+}
+
+// Candidate words: bit i of word t <-> p = 2(32t + i) + 1, set iff p is an
+// odd prime <= the search bound; stored bit-reversed for the clz search.
+int build_candidates()
+{
+    const uint32_t ps = search_pmax();
+    const uint32_t K = (ps + 1) / 2;
+    const uint32_t kw = (K + 31) / 32;
+    std::vector<uint32_t> cand = host_odd_primes(std::max<uint32_t>(ps, 3));
+    std::vector<uint32_t> PR(kw, 0);
+    for (uint32_t p : cand) {
+        if (p > ps) break;
+        uint32_t i = (p - 1) / 2;
+        PR[i / 32] |= 1u << (i % 32);
+    }
+    for (auto &w : PR) w = bitrev32(w);
+    dev_free(&g.d_PR, 4ull * g.k_words);
+    g.k_words = 0;
+    int rc;
+    if ((rc = dev_alloc(&g.d_PR, 4ull * kw))) return rc;
+    g.k_words = kw;
+    CK(cudaMemcpy(g.d_PR, PR.data(), 4ull * kw, cudaMemcpyHostToDevice));
+    g.gkey = GraphKey{};
+    return GB_OK;
 }
 
 int init_locked(uint32_t p_max, uint32_t seg_bits)
@@ -580,21 +739,8 @@ int init_locked(uint32_t p_max, uint32_t seg_bits)
     CK(cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking));
     g.p_max = p_max;
     g.seg_bits = seg_bits;
-    // candidate words: bit i of word t <-> p = 2(32t + i) + 1, set iff p is an
-    // odd prime <= p_max; stored bit-reversed for the clz search
-    const uint32_t K = (p_max + 1) / 2;
-    g.k_words = (K + 31) / 32;
-    std::vector<uint32_t> cand = host_odd_primes(std::max<uint32_t>(p_max, 3));
-    std::vector<uint32_t> PR(g.k_words, 0);
-    for (uint32_t p : cand) {
-        if (p > p_max) break;
-        uint32_t i = (p - 1) / 2;
-        PR[i / 32] |= 1u << (i % 32);
-    }
-    for (auto &w : PR) w = bitrev32(w);
     int rc;
-    if ((rc = dev_alloc(&g.d_PR, 4ull * g.k_words))) return rc;
-    CK(cudaMemcpy(g.d_PR, PR.data(), 4ull * g.k_words, cudaMemcpyHostToDevice));
+    if ((rc = build_candidates())) return rc;
     // bootstrap base primes <= 2^16
     g.h_small = host_odd_primes(1u << 16);
     g.nprimes = g.h_small.size();
@@ -641,6 +787,9 @@ const OptDesc kOpts[] = {
     {"timeout_ms", &Options::timeout_ms, 1, 1ll << 40},
     {"serve_batch_tiles", &Options::serve_batch_tiles, 1, 1 << 24},
     {"time_kernel", &Options::time_kernel, 0, 1},
+    {"bucket_min", &Options::bucket_min, 0, 1 << 22},
+    {"bucket_chunk_tiles", &Options::bucket_chunk_tiles, 1, 8192},
+    {"search_pmax", &Options::search_pmax, 0, 1 << 20},
 };
 
 }  // namespace
@@ -699,13 +848,22 @@ int gb_set_option(const char *key, int64_t value)
             set_error("threads must be 256, 512 or 1024");
             return GB_EINVAL;
         }
+        if (!strcmp(key, "bucket_min") && value != 0 && value < 64) {
+            set_error("bucket_min must be 0 (automatic) or at least 64");
+            return GB_EINVAL;
+        }
         if (!strcmp(key, "wheel") && value != 7 && value != 13) {
             set_error("wheel must be 7 or 13");
+            return GB_EINVAL;
+        }
+        if (!strcmp(key, "search_pmax") && value != 0 && value < 2) {
+            set_error("search_pmax must be 0 (= P_max) or in [2, 2^20]");
             return GB_EINVAL;
         }
         g.opt.*o.field = value;
         g.gkey = GraphKey{};
         if (!strcmp(key, "base_limit") && g.inited && value > 0) return ensure_table((uint64_t)value);
+        if (!strcmp(key, "search_pmax") && g.inited) return build_candidates();
         return GB_OK;
     }
     set_error("unknown option '%s'", key);
@@ -812,6 +970,14 @@ int gb_verify_range_async(uint64_t lo, uint64_t hi, gb_result *dev_out, void *st
     const size_t smem = persistent_smem(tile_bits);
     int grid = 0;
     if ((rc = occupancy_grid(persistent_kernel_ptr((int)g.opt.wheel, nt), nt, smem, &grid))) return rc;
+    if (needs_buckets(cp)) {
+        // the pre-pass sizes its buffers on the host, so this form synchronises
+        rc = run_persistent_buckets(cp, grid, smem, merge_grid_for(cp.nrec), dev_out, st, false);
+        if (rc) return rc;
+        g.stats.calls++;
+        g.stats.n_verified += cp.n_total;
+        return GB_OK;
+    }
     RangeParams p;
     fill_params(cp, tile_bits, p);
     // the params travel as a kernel argument so no host buffer outlives the call

@@ -395,17 +395,53 @@ __device__ __forceinline__ void fixup_pass(uint32_t *win, const WinGeom &g, uint
     }
 }
 
-// Build the whole window (passes 1-3).  Ends with a barrier.
+// Pass 2b: clear the hits of the large primes that the bucket pre-pass
+// scattered to this window (one bit per entry, coalesced entry loads).
+template <int NT>
+__device__ __forceinline__ void bucket_pass(uint32_t *win, const WinGeom &g, const uint32_t *ent,
+                                            unsigned long long b0, unsigned long long b1, Ctrl *ctrl)
+{
+    for (unsigned long long e = b0 + threadIdx.x; e < b1; e += NT) {
+        const uint32_t j = ent[e];
+        if (j < g.j_end) clear_bit(win, j);
+        else atomicOr(&ctrl->flags, F_INTERNAL);          // a bucket entry outside its window
+    }
+}
+
+// Build the whole window (passes 1-3).  Primes from index np_cap on are left
+// to the bucket entries [b0, b1) of ent (none when ent is null).  Ends with a
+// barrier.
 template <int WHEEL, int NT>
 __device__ __forceinline__ void build_window(uint32_t *win, const uint32_t *wpat, const WinGeom &g,
-                                             const Tables &t)
+                                             const Tables &t, uint32_t np_cap = 0xffffffffu,
+                                             const uint32_t *ent = nullptr,
+                                             unsigned long long b0 = 0, unsigned long long b1 = 0,
+                                             Ctrl *ctrl = nullptr)
 {
     fill_pass<WHEEL, NT>(win, wpat, g, t.pat_lo, t.pat_hi);
     __syncthreads();
     uint32_t np = count_le(t.primes, t.nprimes, isqrt_u64(g.q_hi));
+    if (np > np_cap) np = np_cap;
     mark_pass<NT>(win, g, t, np);
+    if (ent) bucket_pass<NT>(win, g, ent, b0, b1, ctrl);
     fixup_pass<WHEEL>(win, g, t.pat_hi);
     __syncthreads();
+}
+
+// First odd multiple of p that is >= max(p^2, w), as a distance from w;
+// w is a window base described by (w mod 2^64, neg).  Returns ~0 when
+// p^2 > q_hi.  Used by the bucket pre-pass (64-bit distances).
+__device__ __forceinline__ unsigned long long first_dist(unsigned long long w, bool neg,
+                                                         unsigned long long q_hi, uint32_t p,
+                                                         unsigned long long m)
+{
+    unsigned long long pp = (unsigned long long)p * p;
+    if (pp > q_hi) return ~0ull;
+    if (neg || pp >= w) return pp - w;
+    uint32_t r = mod_recip(w, p, m);
+    unsigned long long d = r ? (unsigned long long)(p - r) : 0ull;
+    if (d & 1ull) d += p;
+    return d;
 }
 
 // ---------------------------------------------------------------------------

@@ -146,16 +146,21 @@ persistent_kernel(const RangeParams *__restrict__ prm_g, Tables t, DevRec *__res
     const unsigned long long rmask = (1ull << prm.rec_bits) - 1ull;
 
     for (;;) {
-        if (threadIdx.x == 0) s.tile = atomicAdd(&ctrl->tile_ctr, 1ull);
+        if (threadIdx.x == 0) s.tile = prm.tile0 + atomicAdd(&ctrl->tile_ctr, 1ull);
         __syncthreads();
         const unsigned long long tile = s.tile;
-        if (tile >= prm.ntiles) break;
+        if (tile >= prm.tile_end) break;
         const unsigned long long k0 = tile << prm.tile_bits;
         const unsigned long long left = prm.n_total - k0;
         const uint32_t cnt = left < (1ull << prm.tile_bits) ? (uint32_t)left : (1u << prm.tile_bits);
         const unsigned long long n_lo = prm.n0 + 2ull * k0;
         const WinGeom g = tile_geom(n_lo, cnt, 32u * KW);
-        build_window<WHEEL, NT>(win, wpat, g, t);
+        unsigned long long b0 = 0, b1 = 0;
+        if (prm.bk_ent) {
+            b0 = prm.bk_off[tile - prm.tile0];
+            b1 = prm.bk_off[tile - prm.tile0 + 1];
+        }
+        build_window<WHEEL, NT>(win, wpat, g, t, prm.bk_prime0, prm.bk_ent, b0, b1, ctrl);
 
         for (uint32_t ks = 0; ks < cnt; ks += (1u << rbits)) {
             const uint32_t ke = (cnt - ks) < (1u << rbits) ? cnt : ks + (1u << rbits);
@@ -523,6 +528,124 @@ __global__ void exclusive_scan_small_kernel(const uint32_t *__restrict__ in, uin
     }
 }
 
+// ---------------------------------------------------------------------------
+// bucket pre-pass for the large base primes (p >= bucket bound): every hit
+// of such a prime in the windows of tiles [t0, t0 + nt) becomes one entry
+// (window bit index) in that tile's bucket.  Windows overlap by K bits, so a
+// hit in the first K - 1 bits of tile t's window is also a hit in the
+// extension of tile t - 1.
+// ---------------------------------------------------------------------------
+
+struct ChunkGeom {
+    unsigned long long w0;     // window base of tile t0 (mod 2^64)
+    unsigned long long span;   // q_hi of the last tile - w0 (true distance)
+    unsigned long long q_hi;
+    uint32_t S, KB, shift, nt;
+    bool neg;
+};
+
+__device__ __forceinline__ ChunkGeom chunk_geom(const RangeParams &prm, unsigned long long t0, uint32_t nt)
+{
+    ChunkGeom c;
+    c.S = 1u << prm.tile_bits;
+    c.KB = 32u * prm.k_words;
+    c.shift = prm.tile_bits + 1;
+    c.nt = nt;
+    const unsigned long long n_lo0 = prm.n0 + 2ull * (t0 << prm.tile_bits);
+    const unsigned long long h = n_lo0 >> 1;
+    c.neg = h < c.KB;
+    const unsigned long long half_abs = c.neg ? (c.KB - h) : (h - c.KB);
+    c.w0 = c.neg ? (1ull - 2ull * half_abs) : (2ull * half_abs + 1ull);
+    const unsigned long long tl = t0 + nt - 1;
+    const unsigned long long kl = tl << prm.tile_bits;
+    const unsigned long long left = prm.n_total - kl;
+    const unsigned long long cl = left < c.S ? left : c.S;
+    const unsigned long long n_last = prm.n0 + 2ull * (kl + cl - 1ull);
+    c.q_hi = n_last - 1ull;
+    c.span = c.q_hi - c.w0;
+    return c;
+}
+
+template <class F>
+__device__ __forceinline__ void for_each_hit(const ChunkGeom &c, uint32_t p, unsigned long long m, F &&emit)
+{
+    unsigned long long d = first_dist(c.w0, c.neg, c.q_hi, p, m);
+    if (d == ~0ull || d > c.span) return;
+    const unsigned long long step = 2ull * p;
+    for (;;) {
+        // the hit is bit j of tile tt's window and, since consecutive windows
+        // overlap by K - 1 bits, bit j + u S of tile tt - u while that stays
+        // inside a window (j + u S <= S + K - 2); with K > S that is more
+        // than one earlier tile
+        unsigned long long tt = d >> c.shift;
+        uint32_t j = (uint32_t)((d - (tt << c.shift)) >> 1);
+        for (;;) {
+            if (tt < c.nt) emit((uint32_t)tt, j);
+            if (tt == 0ull || j + 1u >= c.KB) break;
+            j += c.S;
+            tt--;
+        }
+        if (c.span - d < step) break;
+        d += step;
+    }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT)
+bucket_count_kernel(const RangeParams *__restrict__ prm_g, Tables t, uint32_t i0, unsigned long long t0,
+                    uint32_t nt, unsigned int *__restrict__ counts)
+{
+    extern __shared__ unsigned int h[];
+    const RangeParams prm = *prm_g;
+    const ChunkGeom c = chunk_geom(prm, t0, nt);
+    const uint32_t i1 = count_le(t.primes, t.nprimes, isqrt_u64(c.q_hi));
+    for (uint32_t k = threadIdx.x; k < nt; k += NT) h[k] = 0u;
+    __syncthreads();
+    for (uint32_t i = i0 + blockIdx.x * NT + threadIdx.x; i < i1; i += gridDim.x * NT)
+        for_each_hit(c, t.primes[i], t.recip[i], [&](uint32_t tt, uint32_t) { atomicAdd(&h[tt], 1u); });
+    __syncthreads();
+    for (uint32_t k = threadIdx.x; k < nt; k += NT)
+        if (h[k]) atomicAdd(&counts[k], h[k]);
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT)
+bucket_fill_kernel(const RangeParams *__restrict__ prm_g, Tables t, uint32_t i0, unsigned long long t0,
+                   uint32_t nt, unsigned int *__restrict__ cursor, uint32_t *__restrict__ ent)
+{
+    extern __shared__ unsigned int h[];
+    const RangeParams prm = *prm_g;
+    const ChunkGeom c = chunk_geom(prm, t0, nt);
+    const uint32_t i1 = count_le(t.primes, t.nprimes, isqrt_u64(c.q_hi));
+    for (uint32_t k = threadIdx.x; k < nt; k += NT) h[k] = 0u;
+    __syncthreads();
+    for (uint32_t i = i0 + blockIdx.x * NT + threadIdx.x; i < i1; i += gridDim.x * NT)
+        for_each_hit(c, t.primes[i], t.recip[i], [&](uint32_t tt, uint32_t) { atomicAdd(&h[tt], 1u); });
+    __syncthreads();
+    // reserve this block's share of every bucket, then write the entries
+    for (uint32_t k = threadIdx.x; k < nt; k += NT)
+        if (h[k]) h[k] = atomicAdd(&cursor[k], h[k]);
+    __syncthreads();
+    for (uint32_t i = i0 + blockIdx.x * NT + threadIdx.x; i < i1; i += gridDim.x * NT)
+        for_each_hit(c, t.primes[i], t.recip[i], [&](uint32_t tt, uint32_t j) {
+            ent[atomicAdd(&h[tt], 1u)] = j;
+        });
+}
+
+// Exclusive scan of the bucket counts (one thread; nt is a few thousand).
+__global__ void bucket_scan_kernel(const unsigned int *__restrict__ counts, uint32_t nt,
+                                   unsigned long long *__restrict__ off, unsigned int *__restrict__ cursor)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    unsigned long long acc = 0;
+    for (uint32_t k = 0; k < nt; k++) {
+        off[k] = acc;
+        cursor[k] = (unsigned int)acc;
+        acc += counts[k];
+    }
+    off[nt] = acc;
+}
+
 __global__ void set_params_kernel(RangeParams *dst, RangeParams p)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) *dst = p;
@@ -531,6 +654,20 @@ __global__ void set_params_kernel(RangeParams *dst, RangeParams p)
 // ---------------------------------------------------------------------------
 // host-side launch wrappers
 // ---------------------------------------------------------------------------
+
+cudaError_t launch_bucket_prepass(cudaStream_t st, int grid, const RangeParams *prm, const Tables &t,
+                                  uint32_t i0, unsigned long long t0, uint32_t nt, unsigned int *counts,
+                                  unsigned long long *off, unsigned int *cursor, uint32_t *ent, int phase)
+{
+    const size_t smem = 4ull * nt;
+    if (phase == 0) {
+        bucket_count_kernel<256><<<grid, 256, smem, st>>>(prm, t, i0, t0, nt, counts);
+        if (cudaPeekAtLastError() == cudaSuccess) bucket_scan_kernel<<<1, 32, 0, st>>>(counts, nt, off, cursor);
+    } else {
+        bucket_fill_kernel<256><<<grid, 256, smem, st>>>(prm, t, i0, t0, nt, cursor, ent);
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t launch_set_params(cudaStream_t st, RangeParams *dst, const RangeParams &p)
 {

@@ -38,4 +38,8 @@ cudaError_t launch_table_compact(cudaStream_t st, const uint32_t *bits, uint32_t
 
 namespace gbk {
 cudaError_t launch_set_params(cudaStream_t st, RangeParams *dst, const RangeParams &p);
+// phase 0: count hits per tile + scan into off/cursor; phase 1: fill entries
+cudaError_t launch_bucket_prepass(cudaStream_t st, int grid, const RangeParams *prm, const Tables &t,
+                                  uint32_t i0, unsigned long long t0, uint32_t nt, unsigned int *counts,
+                                  unsigned long long *off, unsigned int *cursor, uint32_t *ent, int phase);
 }

@@ -262,6 +262,9 @@ extern "C" int gb_verify_range_noalloc(uint64_t lo, uint64_t hi, uint32_t p_max,
     p.k_words = k_words;
     p.p_max = p_max;
     p.slow_cap_log2 = 24;
+    p.bk_prime0 = 0xffffffffu;      // n < 2^40: every base prime is below the bucket bound
+    p.tile0 = 0;
+    p.tile_end = p.ntiles;
     // tables view of the scratch (wheel 13, in-register masks up to 31, lane
     // per prime from 4096 on: index 10 = first prime above 31, 563 = number
     // of odd primes below 4096)

@@ -50,7 +50,11 @@ struct __align__(16) RangeParams {
     unsigned int k_words;              // candidate words (K_bits = 32 k_words)
     unsigned int p_max;
     unsigned int slow_cap_log2;
-    unsigned int pad0;
+    unsigned int bk_prime0;            // primes with index >= this come from buckets
+    unsigned long long tile0;          // this launch processes tiles [tile0, tile_end)
+    unsigned long long tile_end;
+    const unsigned long long *bk_off;  // bucket of tile t: entries [bk_off[t-tile0], bk_off[t-tile0+1])
+    const uint32_t *bk_ent;            // window bit indices; nullptr = no buckets
 };
 
 // Read-only device tables shared by every kernel.
