@@ -121,33 +121,84 @@ class ClockSampler:
 # roofline bookkeeping
 # ---------------------------------------------------------------------------
 
-def algorithmic_smem_words(n_total: int, n_top: int, tile_bits: int, k_words: int,
-                           pattern_max: int) -> dict:
-    """Algorithmic shared-memory word operations of one launch over [4, n_top].
+# Lane-instruction cost of each primitive of the algorithm (the model the
+# roofline counts; see the roofline section of the design notes):
+#   crossing-off mark           4  (word index, bit mask, shared RMW, stride step)
+#   window fill word            4 + in-register pattern primes
+#   bit-parallel step (word, p) 3 + popcount(p)  (shift, and-not, or, plane ors)
+#   word statistics             100 per 32-n word (popcounts over 8 planes)
+#   per-n tail                  20 + 6 per 32-candidate chunk
+MODEL = {"mark": 4, "fill": 4, "step": 3, "word_stats": 100, "tail": 20, "tail_chunk": 6}
+PAT_PRIMES = [11, 13, 17, 19, 23, 29, 31, 37, 41, 43, 47, 53, 59, 61]
 
-    Per even n (tile of S = 2^tile_bits n, window S + K bits):
-      fill   : (S + K)/S / 32 word stores
-      marks  : (S + K)/S * sum over marked primes p <= sqrt(n_top) of 1/p
-               read-modify-writes (each a word read and a word write)
-      search : 2 word loads per warp-chunk step, shared by the 32 lanes;
-               the step count per n is counted by the kernel-independent
-               estimate 1 + P(p_min > 63) (about 1.3 at 1e12)
+
+def odd_primes_upto(x: int):
+    import numpy as np
+    sieve = np.ones(x + 1, dtype=bool)
+    sieve[:2] = False
+    sieve[4::2] = False
+    for i in range(3, int(x ** 0.5) + 1, 2):
+        if sieve[i]:
+            sieve[i * i::2 * i] = False
+    return np.nonzero(sieve)[0][1:]
+
+
+def algorithmic_instructions(n0: int, n_total: int, tile_bits: int, k_words: int, wheel: int,
+                             pattern_max: int, search_chunks: int, p_max: int, hist) -> dict:
+    """Lane instructions the algorithm needs for one launch over n_total even n from n0.
+
+    Marks are counted exactly per prime over [W_0, q_max] (odd multiples from
+    p^2 on); only the K - 1 overlap bits between consecutive windows are
+    added by density.  The tail size comes from the run's own histogram.
     """
     import numpy as np
-    S = 1 << tile_bits
-    K = 32 * k_words
-    ext = (S + K) / S
-    root = int(n_top ** 0.5) + 1
-    sieve = np.ones(root + 1, dtype=bool)
-    sieve[:2] = False
-    for i in range(2, int(root ** 0.5) + 1):
-        if sieve[i]:
-            sieve[i * i::i] = False
-    primes = np.nonzero(sieve)[0]
-    marked = primes[primes > pattern_max]
-    recip = float(np.sum(1.0 / marked))
-    per_n = ext / 32 + 2 * ext * recip + 2 * 1.3 / 32
-    return {"per_n": per_n, "words": per_n * n_total, "sum_inv_p": recip}
+    S, K = 1 << tile_bits, 32 * k_words
+    ntiles = (n_total + S - 1) // S
+    n_last = n0 + 2 * (n_total - 1)
+    q_lo = max(n0 + 1 - 2 * K, 1)
+    q_hi = n_last - 1
+    pat = [q for q in PAT_PRIMES if wheel < q <= pattern_max]
+    bound = max([wheel] + pat)
+    primes = odd_primes_upto(int(q_hi ** 0.5) + 1).astype(np.float64)
+    primes = primes[(primes > bound) & (primes * primes <= q_hi)]
+    start = np.maximum(primes * primes, np.ceil(q_lo / primes) * primes)
+    start = np.where(start % 2 == 0, start + primes, start)
+    marks = float(np.sum(np.maximum(0.0, np.floor((q_hi - start) / (2 * primes)) + 1)))
+    marks += (ntiles - 1) * (K - 1) * float(np.sum(1.0 / primes))
+    words = n_total / 32 + ntiles
+    fill_words = (n_total + ntiles * K) / 32 + ntiles
+    bb = min(64 * search_chunks - 1, p_max) if search_chunks else 0
+    cands = [int(c) for c in odd_primes_upto(max(bb, 3)) if c <= bb]
+    step_cost = sum(MODEL["step"] + bin(c).count("1") for c in cands)
+    tail_n = sum(hist[b] for b in range(len(hist)) if (1 << b) > bb) if search_chunks else n_total
+    instr = (marks * MODEL["mark"] + fill_words * (MODEL["fill"] + len(pat)) + words * step_cost
+             + words * MODEL["word_stats"] * (1 if search_chunks else 0)
+             + tail_n * (MODEL["tail"] + 1.5 * MODEL["tail_chunk"]))
+    return {"instr": instr, "per_n": instr / n_total, "marks_per_n": marks / n_total,
+            "tail_fraction": tail_n / n_total}
+
+
+def csrc_digest() -> str:
+    import hashlib
+    d = os.path.join(ROOT, "paper_2603_07850_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()
+
+
+def measured_traffic(n_count: int):
+    """DRAM bytes per launch of the persistent kernel from the last ncu capture
+    (profiles/persistent_traffic.json), scaled to this launch by even n; None
+    when the kernel sources changed since the capture."""
+    try:
+        t = json.load(open(os.path.join(ROOT, "profiles", "persistent_traffic.json")))
+    except (OSError, ValueError):
+        return None
+    if t.get("csrc_sha256") != csrc_digest():
+        return None
+    return t["dram_bytes"] * n_count / t["n_even"]
 
 
 def load_peaks():
@@ -226,6 +277,7 @@ def run_ours(args):
     gb.load()
     gb.gb_init(P_MAX, SEG_BITS)
     gb.gb_set_option("time_kernel", 1)
+    gb.gb_set_option("autotune", 1)          # the first warm-up step tunes
     lo = rank * args.n_top + 4
     hi = (rank + 1) * args.n_top + 1
     n_total = (hi - 1 - lo) // 2 + 1 if lo % 2 == 0 else None
@@ -306,14 +358,16 @@ def run_ours(args):
         return
 
     peaks = load_peaks()
-    kw = gb.gb_get_option("k_words")
-    alg = algorithmic_smem_words(out["n_count"], args.n_top, gb.gb_get_option("tile_bits"), kw,
-                                 gb.gb_get_option("pattern_max"))
+    opt = {k: gb.gb_get_option(k) for k in ("k_words", "tile_bits", "wheel", "pattern_max",
+                                            "search_chunks", "threads", "sms")}
+    alg = algorithmic_instructions(out["n_first"], out["n_count"], opt["tile_bits"], opt["k_words"],
+                                   opt["wheel"], opt["pattern_max"], opt["search_chunks"], P_MAX,
+                                   out["hist"])
     kus = statistics.mean(kernel_us) if kernel_us else None
     sm_clock = (peaks or {}).get("sm_max_mhz", 2070.0)
-    sms = gb.gb_get_option("sms")
-    peak_words = sms * 32 * sm_clock * 1e6          # 32 banks x 4 B per clock per SM
-    achieved = alg["words"] / (kus * 1e-6) if kus else None
+    peak = opt["sms"] * 128 * sm_clock * 1e6          # 4 schedulers x 32 lanes per SM per clock
+    achieved = alg["instr"] / (kus * 1e-6) if kus else None
+    traffic = measured_traffic(out["n_count"])
     line = {
         "metric": "even n verified/s at N=1e12", "value": tot_n / (ms * 1e-3),
         "unit": "even_n/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -323,16 +377,20 @@ def run_ours(args):
                    "p_max": P_MAX, "seg_bits": SEG_BITS,
                    "tile_bits": gb.gb_get_option("tile_bits"),
                    "threads": gb.gb_get_option("threads"), "wheel": gb.gb_get_option("wheel"),
+                   "search_chunks": gb.gb_get_option("search_chunks"),
                    "l2": "flushed between steps (512 MB write)", "form": "persistent"},
         "e2e": {"value": tot_n / e2e_s, "unit": "even_n/s", "h2d_bytes_per_step": 64,
                 "d2h_bytes_per_step": gb.RESULT_BYTES},
         "gpu_launches": 4 * args.steps,
         "clocks": clocks,
         "roofline": {"bound": "alu", "achieved": achieved / 1e9 if achieved else None,
-                     "peak": peak_words / 1e9, "unit": "Gword/s",
-                     "frac": (achieved / peak_words) if achieved else None, "traffic": None,
-                     "kernel_us": kus, "per_n_words": alg["per_n"],
-                     "peak_note": "shared-memory bank slots: SMs x 32 x max SM clock"},
+                     "peak": peak / 1e9, "unit": "Ginstr/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "kernel": "persistent_kernel", "kernel_us": kus,
+                     "algorithmic_instr_per_n": alg["per_n"], "marks_per_n": alg["marks_per_n"],
+                     "tail_fraction": alg["tail_fraction"],
+                     "peak_note": "issue slots: SMs x 4 schedulers x 32 lanes x max SM clock "
+                                  "(derived, of measured clock)"},
         "plain": plain,
         "speedup_vs_plain": (tot_n / (ms * 1e-3)) / plain["value"] if plain else None,
         "result": {k: out[k] for k in ("n_count", "max_pmin", "argmax_n", "sum_pmin", "n_slow")},

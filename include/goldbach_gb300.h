@@ -72,6 +72,8 @@ typedef struct {
     uint64_t counterexample_n; /* smallest counterexample found, 0 if none     */
     int32_t  status;           /* same value the call returned                 */
     int32_t  reserved;
+    uint64_t submit_ns;        /* served requests: host steady-clock time of gb_submit, else 0 */
+    uint64_t done_ns;          /* served requests: time the result reached the host, else 0 */
 } gb_result;
 
 /* One report segment: 2^seg_bits consecutive even n (the last one of a range
@@ -127,7 +129,7 @@ int gb_init(uint32_t p_max, uint32_t seg_bits);
 /*
  * gb_set_option -- tune the context.  Keys (value range):
  *   "tile_bits"     log2 even n per sieve tile, 10..20 (default 20)
- *   "threads"       threads per CTA: 256, 512 or 1024 (default 512)
+ *   "threads"       threads per CTA: 256, 512 or 1024 (default 1024)
  *   "ctas_per_sm"   persistent CTAs per SM, 1..4 (default: as many as fit)
  *   "wheel"         largest wheel prime pre-sieved by pattern: 7 or 13 (default 13)
  *   "pattern_max"   largest prime cleared by in-register patterns, 13..61 (default 31)
@@ -140,6 +142,15 @@ int gb_init(uint32_t p_max, uint32_t seg_bits);
  *   "tier_b_min"    smallest prime crossed off lane-per-prime (default 4096)
  *   "plain_slice_bits" log2 window bits per CTA in the plain sieve kernel (default 18)
  *   "time_kernel"   1 = time the persistent kernel with CUDA events (default 0)
+ *   "search_chunks" bit-parallel search over the candidates p < 64 * this: 2, 3 or 4
+ *                   (default 4); 0 = one lane per n (wheel 7 allows 0, 3, 4)
+ *   "serve_batch_tiles" tiles per serving launch (default 1024)
+ *   "autotune"      1 = before the first call of each range class (GPU, P_max,
+ *                   log2 of the largest n), time the kernel configurations on a
+ *                   probe at the top of the range and keep the fastest (tile_bits,
+ *                   threads, search_chunks, pattern_max, search_pmax); the choice
+ *                   is cached, and saved to the file named by GB_TUNE_CACHE if set.
+ *                   The tuning call synchronises.  Results never depend on it.
  *   "search_pmax"   bound of the in-window candidate search, 0 = P_max (default 0);
  *                   n with p_min above it take the slow path, but n_slow and
  *                   every other output still refer to P_max

@@ -34,6 +34,7 @@ class GbResult(ctypes.Structure):
         ("n_first", U64), ("n_count", U64), ("max_pmin", U64), ("argmax_n", U64),
         ("sum_pmin", U64), ("wsum_pmin", U64), ("hist", U64 * 64), ("n_slow", U64),
         ("counterexample_n", U64), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("submit_ns", U64), ("done_ns", U64),
     ]
 
     def as_dict(self) -> dict:

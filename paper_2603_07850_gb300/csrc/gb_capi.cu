@@ -37,7 +37,7 @@ namespace {
 
 struct Options {
     int64_t tile_bits = 20;
-    int64_t threads = 512;
+    int64_t threads = 1024;
     int64_t ctas_per_sm = 0;       // 0 = as many as fit
     int64_t wheel = 13;
     int64_t pattern_max = 31;
@@ -49,11 +49,13 @@ struct Options {
     int64_t use_graph = 1;
     int64_t slow_cap = 24;
     int64_t timeout_ms = 600000;
-    int64_t serve_batch_tiles = 4096;
+    int64_t serve_batch_tiles = 1024;
     int64_t time_kernel = 0;       // record CUDA events around the persistent kernel
     int64_t bucket_min = 0;        // smallest bucketed prime; 0 = the window span S + K
     int64_t bucket_chunk_tiles = 2048;
     int64_t search_pmax = 0;       // window search bound; 0 = P_max
+    int64_t search_chunks = 4;     // bit-parallel search over p < 64 * this (0 = per-n search)
+    int64_t autotune = 0;          // 1: tune the kernel configuration per range class
 };
 
 struct GraphKey {
@@ -108,11 +110,16 @@ struct Ctx {
     uint32_t *d_bk_ent = nullptr;
     size_t bk_ent_cap = 0;
     std::map<uint64_t, uint32_t> odd_primes_below;  // cache: bound -> #odd primes below it
+    char dev_name[256] = {0};
+    struct TuneCfg { int64_t tile_bits, threads, search_chunks, pattern_max, search_pmax; };
+    std::map<std::string, TuneCfg> tuned;       // autotuner results by range class
     bool ev_pending = false;
 };
 
 Ctx g;
+std::atomic<bool> g_ready{false};        // gb_init done: readable without the context lock
 uint32_t search_pmax();
+int build_candidates();
 std::recursive_mutex g_mu;
 std::mutex g_err_mu;
 std::string g_err = "";
@@ -271,6 +278,7 @@ int ensure_table(uint64_t need)
             (rc = dev_alloc(&nr, 8ull * total)) == GB_OK) {
             e = launch_table_compact(g.stream, bits, gwords, bc, bo, L, np, nr, 0);
             if (e == cudaSuccess) e = cudaStreamSynchronize(g.stream);
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();   // no launch may still read the old table
             if (e == cudaSuccess) {
                 dev_free(&g.d_primes, 4ull * g.nprimes);
                 dev_free(&g.d_recip, 8ull * g.nprimes);
@@ -366,6 +374,11 @@ int prepare_common(const CallPlan &cp)
 
 int occupancy_grid(const void *fn, int nt, size_t smem, int *grid)
 {
+    if (!fn) {
+        set_error("no kernel for this combination of wheel, threads and search_chunks "
+                  "(wheel 7 supports search_chunks 0, 3, 4)");
+        return GB_EINVAL;
+    }
     CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nt, smem));
@@ -396,7 +409,7 @@ int enqueue_persistent(cudaStream_t st, const CallPlan &cp, gb_result *dev_out, 
         if (!g.ev1) CK(cudaEventCreate(&g.ev1));
         CK(cudaEventRecord(g.ev0, st));
     }
-    CK(launch_persistent((int)g.opt.wheel, (int)g.opt.threads, grid, smem, st, g.d_params, t, g.d_recs,
+    CK(launch_persistent((int)g.opt.wheel, (int)g.opt.threads, (int)g.opt.search_chunks, grid, smem, st, g.d_params, t, g.d_recs,
                          g.d_ctrl));
     if (timed) {
         CK(cudaEventRecord(g.ev1, st));
@@ -489,7 +502,7 @@ int run_persistent_buckets(const CallPlan &cp, int grid, size_t smem, int mg, gb
         p.bk_ent = g.d_bk_ent;
         CK(launch_set_params(st, g.d_params, p));
         CK(cudaMemsetAsync(&g.d_ctrl->tile_ctr, 0, 8, st));
-        CK(launch_persistent((int)g.opt.wheel, (int)g.opt.threads, grid, smem, st, g.d_params, t, g.d_recs,
+        CK(launch_persistent((int)g.opt.wheel, (int)g.opt.threads, (int)g.opt.search_chunks, grid, smem, st, g.d_params, t, g.d_recs,
                              g.d_ctrl));
         launches += 5;
     }
@@ -507,16 +520,155 @@ int run_persistent_buckets(const CallPlan &cp, int grid, size_t smem, int mg, gb
     return GB_OK;
 }
 
+// ---------------------------------------------------------------------------
+// autotuner: coordinate descent over the kernel configuration, timed with
+// CUDA events on a probe at the top of the caller's range; results cached per
+// (GPU, SMs, P_max, log2 of the largest n rounded to even) in memory and, when
+// GB_TUNE_CACHE names a file, on disk.
+// ---------------------------------------------------------------------------
+
+using TuneCfg = Ctx::TuneCfg;
+
+TuneCfg current_cfg()
+{
+    return TuneCfg{g.opt.tile_bits, g.opt.threads, g.opt.search_chunks, g.opt.pattern_max,
+                   g.opt.search_pmax};
+}
+
+int apply_cfg(const TuneCfg &c)
+{
+    const bool pr = c.search_pmax != g.opt.search_pmax;
+    g.opt.tile_bits = c.tile_bits;
+    g.opt.threads = c.threads;
+    g.opt.search_chunks = c.search_chunks;
+    g.opt.pattern_max = c.pattern_max;
+    g.opt.search_pmax = c.search_pmax;
+    g.gkey = GraphKey{};
+    return pr ? build_candidates() : GB_OK;
+}
+
+std::string tune_key(const CallPlan &cp)
+{
+    const uint64_t n_last = cp.n0 + 2 * (cp.n_total - 1);
+    const int mag = 63 - __builtin_clzll(n_last);
+    char buf[400];
+    snprintf(buf, sizeof buf, "%s|sm%d|pmax%u|log2n%d", g.dev_name, g.sms, g.p_max, mag & ~1);
+    for (char *c = buf; *c; c++)
+        if (*c == ' ') *c = '_';
+    return buf;
+}
+
+// Kernel time of one persistent launch over the probe range; < 0 if the
+// configuration cannot run.
+float time_probe(const CallPlan &probe_in)
+{
+    CallPlan probe = probe_in;
+    probe.ntiles = ((probe.n_total - 1) >> g.opt.tile_bits) + 1;
+    const int nt = (int)g.opt.threads;
+    const size_t smem = persistent_smem((uint32_t)g.opt.tile_bits);
+    const void *fn = persistent_kernel_ptr((int)g.opt.wheel, nt, (int)g.opt.search_chunks);
+    if (!fn || smem > g.smem_optin) return -1.f;
+    int grid = 0;
+    if (occupancy_grid(fn, nt, smem, &grid)) { cudaGetLastError(); return -1.f; }
+    RangeParams p;
+    fill_params(probe, (uint32_t)g.opt.tile_bits, p);
+    float best = -1.f;
+    for (int rep = 0; rep < 2; rep++) {
+        if (launch_set_params(g.stream, g.d_params, p) != cudaSuccess) return -1.f;
+        if (enqueue_persistent(g.stream, probe, g.d_result, grid, smem, merge_grid_for(probe.nrec), true))
+            return -1.f;
+        if (cudaStreamSynchronize(g.stream) != cudaSuccess) return -1.f;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, g.ev0, g.ev1) != cudaSuccess) return -1.f;
+        if (best < 0 || ms < best) best = ms;
+    }
+    return best;
+}
+
+void load_tune_file()
+{
+    const char *path = getenv("GB_TUNE_CACHE");
+    if (!path) return;
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    char key[400];
+    long long a, b, c, d, e;
+    while (fscanf(f, "%399s %lld %lld %lld %lld %lld", key, &a, &b, &c, &d, &e) == 6)
+        g.tuned[key] = TuneCfg{a, b, c, d, e};
+    fclose(f);
+}
+
+void save_tune_file()
+{
+    const char *path = getenv("GB_TUNE_CACHE");
+    if (!path) return;
+    FILE *f = fopen(path, "w");
+    if (!f) return;
+    for (const auto &kv : g.tuned)
+        fprintf(f, "%s %lld %lld %lld %lld %lld\n", kv.first.c_str(), (long long)kv.second.tile_bits,
+                (long long)kv.second.threads, (long long)kv.second.search_chunks,
+                (long long)kv.second.pattern_max, (long long)kv.second.search_pmax);
+    fclose(f);
+}
+
+// Pick (and cache) the configuration for cp's range class; cp.ntiles follows
+// the chosen tile size.
+int maybe_autotune(CallPlan &cp)
+{
+    if (!g.opt.autotune || needs_buckets(cp)) return GB_OK;
+    if (g.tuned.empty()) load_tune_file();
+    const std::string key = tune_key(cp);
+    auto it = g.tuned.find(key);
+    int rc;
+    if (it == g.tuned.end()) {
+        CallPlan probe;
+        probe.n_total = std::min<uint64_t>(cp.n_total, 1ull << 30);
+        probe.n0 = cp.n0 + 2 * (cp.n_total - probe.n_total);
+        probe.nrec = ((probe.n_total - 1) >> g.seg_bits) + 1;
+        if ((rc = ensure_records(probe.nrec))) return rc;
+        TuneCfg best = current_cfg();
+        float best_ms = time_probe(probe);
+        const std::vector<std::pair<int64_t TuneCfg::*, std::vector<int64_t>>> axes = {
+            {&TuneCfg::search_chunks, {2, 3, 4}},
+            {&TuneCfg::threads, {512, 1024}},
+            {&TuneCfg::tile_bits, {18, 19, 20}},
+            {&TuneCfg::pattern_max, {13, 31, 61}},
+            {&TuneCfg::search_pmax, {0, 4096}},
+        };
+        for (int pass = 0; pass < 2; pass++) {
+            for (const auto &ax : axes) {
+                for (int64_t v : ax.second) {
+                    TuneCfg c = best;
+                    c.*(ax.first) = v;
+                    if (c.*(ax.first) == best.*(ax.first)) continue;
+                    if (c.search_pmax && c.search_pmax >= (int64_t)g.p_max) continue;
+                    if ((rc = apply_cfg(c))) return rc;
+                    const float ms = time_probe(probe);
+                    if (ms > 0.f && (best_ms < 0.f || ms < 0.99f * best_ms)) { best = c; best_ms = ms; }
+                }
+            }
+        }
+        if ((rc = apply_cfg(best))) return rc;
+        g.tuned[key] = best;
+        save_tune_file();
+    } else if ((rc = apply_cfg(it->second))) {
+        return rc;
+    }
+    cp.ntiles = ((cp.n_total - 1) >> g.opt.tile_bits) + 1;
+    return GB_OK;
+}
+
 int run_persistent(uint64_t lo, uint64_t hi, CallPlan &cp)
 {
     int rc = plan_range(lo, hi, cp);
     if (rc) return rc;
     if (!cp.n_total) return GB_OK;
     if ((rc = prepare_common(cp))) return rc;
+    if ((rc = maybe_autotune(cp))) return rc;
     const uint32_t tile_bits = (uint32_t)g.opt.tile_bits;
     const int nt = (int)g.opt.threads;
     const size_t smem = persistent_smem(tile_bits);
-    const void *fn = persistent_kernel_ptr((int)g.opt.wheel, nt);
+    const void *fn = persistent_kernel_ptr((int)g.opt.wheel, nt, (int)g.opt.search_chunks);
     int grid = 0;
     if ((rc = occupancy_grid(fn, nt, smem, &grid))) return rc;
     const int mg = merge_grid_for(cp.nrec);
@@ -665,7 +817,9 @@ int run_plain(uint64_t lo, uint64_t hi, CallPlan &cp)
 
 void release_all()
 {
+    g_ready = false;
     serve_stop();
+    ctx_serve_end();
     if (g.gexec) { cudaGraphExecDestroy(g.gexec); g.gexec = nullptr; }
     g.gkey = GraphKey{};
     dev_free(&g.d_primes, 4ull * g.nprimes);
@@ -735,6 +889,7 @@ int init_locked(uint32_t p_max, uint32_t seg_bits)
     cudaDeviceProp prop;
     CK(cudaGetDeviceProperties(&prop, g.device));
     g.sms = prop.multiProcessorCount;
+    snprintf(g.dev_name, sizeof g.dev_name, "%s", prop.name);
     g.smem_optin = prop.sharedMemPerBlockOptin;
     CK(cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking));
     g.p_max = p_max;
@@ -761,6 +916,7 @@ int init_locked(uint32_t p_max, uint32_t seg_bits)
     CK(cudaMallocHost((void **)&g.h_flags, 4));
     memset(&g.stats, 0, sizeof g.stats);
     g.inited = true;
+    g_ready = true;
     if (g.opt.base_limit > 0 && (rc = ensure_table((uint64_t)g.opt.base_limit))) return rc;
     return GB_OK;
 }
@@ -790,6 +946,8 @@ const OptDesc kOpts[] = {
     {"bucket_min", &Options::bucket_min, 0, 1 << 22},
     {"bucket_chunk_tiles", &Options::bucket_chunk_tiles, 1, 8192},
     {"search_pmax", &Options::search_pmax, 0, 1 << 20},
+    {"search_chunks", &Options::search_chunks, 0, 4},
+    {"autotune", &Options::autotune, 0, 1},
 };
 
 }  // namespace
@@ -799,11 +957,13 @@ const OptDesc kOpts[] = {
 // ---------------------------------------------------------------------------
 namespace gbk {
 std::recursive_mutex &ctx_mutex() { return g_mu; }
-bool ctx_ready() { return g.inited; }
+bool ctx_ready() { return g_ready.load(); }
+// Options are plain aligned 64-bit values: read without the context lock so
+// that gb_submit never waits for a running batch.
 int64_t ctx_option(const char *key)
 {
     for (const auto &o : kOpts)
-        if (!strcmp(o.key, key)) return g.opt.*o.field;
+        if (!strcmp(o.key, key)) return __atomic_load_n(&(g.opt.*o.field), __ATOMIC_RELAXED);
     return 0;
 }
 int ctx_verify(uint64_t lo, uint64_t hi, gb_result *out)
@@ -819,6 +979,169 @@ int ctx_verify(uint64_t lo, uint64_t hi, gb_result *out)
 void ctx_error(const char *msg) { set_error("%s", msg); }
 gb_stats_t &ctx_stats() { return g.stats; }
 size_t ctx_device_bytes() { return g.device_bytes; }
+
+// ---- serving engine state (device side of gb_submit / gb_poll) -------------
+namespace {
+struct ServeDev {
+    bool ready = false;
+    int max_slots = 0, max_items = 0;
+    cudaStream_t st = nullptr, cp = nullptr;     // batches; harvest copies
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    SlotDev *d_slots = nullptr, *h_slots = nullptr;
+    unsigned long long *d_items[2] = {nullptr, nullptr}, *h_items[2] = {nullptr, nullptr};
+    Ctrl *d_ctrl = nullptr;
+    unsigned int *h_flags = nullptr;
+    const void *fn = nullptr;
+    int nt = 0, grid = 0;
+    size_t smem = 0;
+};
+ServeDev sv;
+}  // namespace
+
+int ctx_serve_begin(int max_slots, int max_items)
+{
+    if (sv.ready) return GB_OK;
+    int rc;
+    sv.max_slots = max_slots;
+    sv.max_items = max_items;
+    CK(cudaStreamCreateWithFlags(&sv.st, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&sv.cp, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&sv.ev[0], cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&sv.ev[1], cudaEventDisableTiming));
+    if ((rc = dev_alloc(&sv.d_slots, sizeof(SlotDev) * max_slots))) return rc;
+    if ((rc = dev_alloc(&sv.d_ctrl, sizeof(Ctrl)))) return rc;
+    CK(cudaMallocHost((void **)&sv.h_slots, sizeof(SlotDev) * max_slots));
+    CK(cudaMallocHost((void **)&sv.h_flags, 4));
+    for (int b = 0; b < 2; b++) {
+        if ((rc = dev_alloc(&sv.d_items[b], 8ull * max_items))) return rc;
+        CK(cudaMallocHost((void **)&sv.h_items[b], 8ull * max_items));
+    }
+    // kernel configuration: the context's, when a serving instantiation exists
+    sv.nt = (int)g.opt.threads;
+    int wheel = (int)g.opt.wheel, bc = (int)g.opt.search_chunks;
+    sv.fn = serve_kernel_ptr(wheel, sv.nt, bc);
+    if (!sv.fn) { sv.nt = 512; sv.fn = serve_kernel_ptr(13, 512, 3); }
+    sv.smem = persistent_smem((uint32_t)g.opt.tile_bits);
+    if ((rc = occupancy_grid(sv.fn, sv.nt, sv.smem, &sv.grid))) return rc;
+    sv.ready = true;
+    return GB_OK;
+}
+
+void ctx_serve_end()
+{
+    if (!sv.ready) return;
+    cudaStreamSynchronize(sv.st);
+    cudaStreamSynchronize(sv.cp);
+    dev_free(&sv.d_slots, sizeof(SlotDev) * sv.max_slots);
+    dev_free(&sv.d_ctrl, sizeof(Ctrl));
+    for (int b = 0; b < 2; b++) {
+        dev_free(&sv.d_items[b], 8ull * sv.max_items);
+        if (sv.h_items[b]) cudaFreeHost(sv.h_items[b]);
+        if (sv.ev[b]) cudaEventDestroy(sv.ev[b]);
+    }
+    if (sv.h_slots) cudaFreeHost(sv.h_slots);
+    if (sv.h_flags) cudaFreeHost(sv.h_flags);
+    if (sv.st) cudaStreamDestroy(sv.st);
+    if (sv.cp) cudaStreamDestroy(sv.cp);
+    sv = ServeDev{};
+}
+
+// Validate a request and make sure the base-prime table covers it.  The
+// caller has no batch in flight when the table may have to grow.
+int ctx_serve_plan(uint64_t lo, uint64_t hi, ServePlan *sp)
+{
+    CallPlan cp;
+    int rc = plan_range(lo, hi, cp);
+    if (rc) return rc;
+    sp->n0 = cp.n0;
+    sp->n_total = cp.n_total;
+    sp->ntiles = cp.ntiles;
+    if (!cp.n_total) return GB_OK;
+    if (cp.n_total >= (1ull << SERVE_SLOT_SHIFT)) {
+        set_error("a served request must hold fewer than 2^40 even n");
+        return GB_EINVAL;
+    }
+    return ensure_table(isqrt_host(cp.n0 + 2 * (cp.n_total - 1)));
+}
+
+bool ctx_serve_needs_table(uint64_t lo, uint64_t hi)
+{
+    CallPlan cp;
+    if (plan_range(lo, hi, cp) || !cp.n_total) return false;
+    return isqrt_host(cp.n0 + 2 * (cp.n_total - 1)) > g.table_limit;
+}
+
+int ctx_serve_init_slot(int slot, const ServePlan &sp)
+{
+    SlotDev &h = sv.h_slots[slot];
+    memset(&h, 0, sizeof h);
+    CallPlan cp;
+    cp.n0 = sp.n0;
+    cp.n_total = sp.n_total;
+    cp.ntiles = sp.ntiles;
+    cp.nrec = 1;
+    fill_params(cp, (uint32_t)g.opt.tile_bits, h.prm);
+    h.prm.rec_bits = SERVE_SLOT_SHIFT;
+    CK(cudaMemcpyAsync(&sv.d_slots[slot], &h, sizeof h, cudaMemcpyHostToDevice, sv.st));
+    return GB_OK;
+}
+
+unsigned long long *ctx_serve_items(int buf) { return sv.h_items[buf]; }
+
+int ctx_serve_launch(int buf, size_t n)
+{
+    CK(cudaMemcpyAsync(sv.d_items[buf], sv.h_items[buf], 8ull * n, cudaMemcpyHostToDevice, sv.st));
+    CK(cudaMemsetAsync(sv.d_ctrl, 0, sizeof(Ctrl), sv.st));
+    Tables t = make_tables();
+    CK(launch_serve(sv.fn, sv.nt, sv.grid, sv.smem, sv.st, sv.d_items[buf], n, sv.d_slots, t, sv.d_ctrl));
+    CK(cudaEventRecord(sv.ev[buf], sv.st));
+    g.stats.kernel_launches += 1;
+    g.stats.tiles += n;
+    return GB_OK;
+}
+
+// Wait for batch buf and read its status flags.  Touches only the serving
+// streams and buffers, so the caller does not hold the context lock.
+int ctx_serve_wait(int buf, unsigned int *flags)
+{
+    CK(cudaStreamWaitEvent(sv.cp, sv.ev[buf], 0));
+    CK(cudaMemcpyAsync(sv.h_flags, &sv.d_ctrl->flags, 4, cudaMemcpyDeviceToHost, sv.cp));
+    CK(cudaStreamSynchronize(sv.cp));
+    *flags = *sv.h_flags;
+    return GB_OK;
+}
+
+// Copy a finished request's record out (its last batch has completed);
+// called without the context lock.
+int ctx_serve_fetch(int slot, const ServePlan &sp, unsigned int flags, gb_result *out)
+{
+    DevRec *h = &sv.h_slots[slot].acc;
+    CK(cudaMemcpyAsync(h, &sv.d_slots[slot].acc, sizeof(DevRec), cudaMemcpyDeviceToHost, sv.cp));
+    CK(cudaStreamSynchronize(sv.cp));
+    memset(out, 0, sizeof *out);
+    out->n_first = sp.n0;
+    out->n_count = h->n_count;
+    out->max_pmin = h->key >> KEY_SHIFT;
+    out->argmax_n = h->key ? sp.n0 + 2 * (KEY_KMASK - (h->key & KEY_KMASK)) : 0;
+    out->sum_pmin = h->sum;
+    out->wsum_pmin = h->wsum;
+    for (int b = 0; b < HIST_BINS; b++) out->hist[b] = h->hist[b];
+    out->n_slow = h->n_slow;
+    out->counterexample_n = h->ce_inv ? ~h->ce_inv : 0;
+    int st = GB_OK;
+    if (flags & F_INTERNAL) st = GB_EINTERNAL;
+    else if (flags & F_SLOWCAP) st = GB_ESLOWPATH_LIMIT;
+    else if (flags & F_OVERFLOW) st = GB_EOVERFLOW;
+    else if (out->counterexample_n) st = GB_COUNTEREXAMPLE;
+    out->status = st;
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    g.stats.calls++;
+    g.stats.n_verified += sp.n_total;
+    g.stats.n_slow += out->n_slow;
+    return GB_OK;
+}
+
+size_t ctx_serve_slot_bytes() { return sizeof(SlotDev); }
 }  // namespace gbk
 
 // ---------------------------------------------------------------------------
@@ -828,6 +1151,7 @@ extern "C" {
 
 int gb_init(uint32_t p_max, uint32_t seg_bits)
 {
+    serve_stop();                    // before the context lock: the loop takes it
     std::lock_guard<std::recursive_mutex> lk(g_mu);
     int rc = init_locked(p_max, seg_bits);
     if (rc && g.inited) release_all();
@@ -850,6 +1174,10 @@ int gb_set_option(const char *key, int64_t value)
         }
         if (!strcmp(key, "bucket_min") && value != 0 && value < 64) {
             set_error("bucket_min must be 0 (automatic) or at least 64");
+            return GB_EINVAL;
+        }
+        if (!strcmp(key, "search_chunks") && value == 1) {
+            set_error("search_chunks must be 0 (per-n search) or 2..4");
             return GB_EINVAL;
         }
         if (!strcmp(key, "wheel") && value != 7 && value != 13) {
@@ -898,6 +1226,7 @@ int gb_get_option(const char *key, int64_t *value)
 
 void gb_shutdown(void)
 {
+    serve_stop();                    // before the context lock: the loop takes it
     std::lock_guard<std::recursive_mutex> lk(g_mu);
     if (g.inited) release_all();
 }
@@ -965,11 +1294,12 @@ int gb_verify_range_async(uint64_t lo, uint64_t hi, gb_result *dev_out, void *st
         return GB_OK;
     }
     if ((rc = prepare_common(cp))) return rc;
+    if ((rc = maybe_autotune(cp))) return rc;          // synchronises while it tunes
     const uint32_t tile_bits = (uint32_t)g.opt.tile_bits;
     const int nt = (int)g.opt.threads;
     const size_t smem = persistent_smem(tile_bits);
     int grid = 0;
-    if ((rc = occupancy_grid(persistent_kernel_ptr((int)g.opt.wheel, nt), nt, smem, &grid))) return rc;
+    if ((rc = occupancy_grid(persistent_kernel_ptr((int)g.opt.wheel, nt, (int)g.opt.search_chunks), nt, smem, &grid))) return rc;
     if (needs_buckets(cp)) {
         // the pre-pass sizes its buffers on the host, so this form synchronises
         rc = run_persistent_buckets(cp, grid, smem, merge_grid_for(cp.nrec), dev_out, st, false);

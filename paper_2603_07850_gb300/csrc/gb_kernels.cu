@@ -18,186 +18,9 @@
 
 #include "gb_device.cuh"
 #include "gb_kernels.h"
+#include "gb_persist.cuh"
 
 namespace gbk {
-
-// ---------------------------------------------------------------------------
-// persistent fused kernel
-// ---------------------------------------------------------------------------
-
-struct RedScratch {
-    unsigned long long arg[32], sum[32], wsum[32], ce[32];
-    uint32_t mx[32], slow[32];
-    uint32_t hist[HIST_BINS];
-    unsigned long long tile;
-};
-
-// Fold one p_min into a lane's running record state.
-struct LaneAcc {
-    uint32_t mx, slow;
-    unsigned long long arg, sum, wsum, ce, hA, hB;
-    __device__ __forceinline__ void reset()
-    {
-        mx = 0; slow = 0; arg = ~0ull; sum = 0; wsum = 0; ce = 0; hA = 0; hB = 0;
-    }
-    __device__ __forceinline__ void add(uint32_t pm, unsigned long long kr, uint32_t p_max,
-                                        uint32_t *s_hist)
-    {
-        if (pm > mx) { mx = pm; arg = kr; }           // k ascends per lane: first max wins
-        sum += pm;
-        wsum += (unsigned long long)pm * (kr + 1ull);
-        slow += pm > p_max ? 1u : 0u;
-        uint32_t b = 31u - __clz(pm);                 // floor(log2 p_min) >= 1
-        if (b <= 4) hA += 1ull << (16u * (b - 1u));
-        else if (b <= 8) hB += 1ull << (16u * (b - 5u));
-        else atomicAdd(&s_hist[b], 1u);
-    }
-};
-
-// CTA-wide reduction of the lanes' state into record r.  `whole` = the tile
-// owns the record (plain stores) instead of sharing it (atomics).
-template <int NT>
-__device__ __forceinline__ void reduce_to_record(LaneAcc &a, RedScratch &s, DevRec *rec,
-                                                 uint32_t n_cnt, bool whole, Ctrl *ctrl)
-{
-    constexpr int NWARP = NT / 32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t wmax = __reduce_max_sync(GB_FULL_MASK, a.mx);
-    unsigned long long warg = warp_min_u64(a.mx == wmax ? a.arg : ~0ull);
-    unsigned long long wsum = warp_sum_u64(a.sum), wws = warp_sum_u64(a.wsum);
-    unsigned long long wce = a.ce;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        unsigned long long v = __shfl_xor_sync(GB_FULL_MASK, wce, o);
-        wce = v > wce ? v : wce;
-    }
-    uint32_t wslow = __reduce_add_sync(GB_FULL_MASK, a.slow);
-#pragma unroll
-    for (int f = 0; f < 4; f++) {
-        uint32_t ca = __reduce_add_sync(GB_FULL_MASK, (uint32_t)(a.hA >> (16 * f)) & 0xffffu);
-        uint32_t cb = __reduce_add_sync(GB_FULL_MASK, (uint32_t)(a.hB >> (16 * f)) & 0xffffu);
-        if (lane == 0) {
-            if (ca) atomicAdd(&s.hist[1 + f], ca);
-            if (cb) atomicAdd(&s.hist[5 + f], cb);
-        }
-    }
-    if (lane == 0) {
-        s.mx[warp] = wmax; s.arg[warp] = warg; s.sum[warp] = wsum; s.wsum[warp] = wws;
-        s.slow[warp] = wslow; s.ce[warp] = wce;
-    }
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t m = lane < NWARP ? s.mx[lane] : 0u;
-        unsigned long long ar = lane < NWARP ? s.arg[lane] : ~0ull;
-        uint32_t cm = __reduce_max_sync(GB_FULL_MASK, m);
-        unsigned long long ca = warp_min_u64(m == cm ? ar : ~0ull);
-        unsigned long long su = warp_sum_u64(lane < NWARP ? s.sum[lane] : 0ull);
-        unsigned long long ws = warp_sum_u64(lane < NWARP ? s.wsum[lane] : 0ull);
-        uint32_t sl = __reduce_add_sync(GB_FULL_MASK, lane < NWARP ? s.slow[lane] : 0u);
-        unsigned long long ce = lane < NWARP ? s.ce[lane] : 0ull;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            unsigned long long v = __shfl_xor_sync(GB_FULL_MASK, ce, o);
-            ce = v > ce ? v : ce;
-        }
-        unsigned long long key = cm ? (((unsigned long long)cm << KEY_SHIFT) | (KEY_KMASK - ca)) : 0ull;
-        if (whole) {
-            if (lane == 0) {
-                rec->key = key; rec->sum = su; rec->wsum = ws; rec->n_count = n_cnt;
-                rec->n_slow = sl; rec->ce_inv = ce;
-            }
-            rec->hist[lane] = s.hist[lane];
-        } else {
-            if (lane == 0) {
-                if (key) atomicMax(&rec->key, key);
-                atomicAdd(&rec->sum, su);
-                atomicAdd(&rec->wsum, ws);
-                atomicAdd(&rec->n_count, (unsigned long long)n_cnt);
-                if (sl) atomicAdd(&rec->n_slow, (unsigned long long)sl);
-                if (ce) atomicMax(&rec->ce_inv, ce);
-            }
-            if (s.hist[lane]) atomicAdd(&rec->hist[lane], (unsigned long long)s.hist[lane]);
-        }
-        if (lane == 0 && sl) atomicAdd(&ctrl->slow_total, (unsigned long long)sl);
-    }
-}
-
-template <int WHEEL, int NT>
-__global__ void __launch_bounds__(NT, 1)
-persistent_kernel(const RangeParams *__restrict__ prm_g, Tables t, DevRec *__restrict__ recs,
-                  Ctrl *ctrl)
-{
-    extern __shared__ __align__(16) uint32_t smem[];
-    __shared__ RedScratch s;
-    constexpr int NWARP = NT / 32;
-    constexpr uint32_t WP = ((WheelM<WHEEL>::M + 64 + 31) / 32 + 3) & ~3u;
-    const RangeParams prm = *prm_g;
-    const uint32_t KW = prm.k_words;
-    uint32_t *wpat = smem;
-    uint32_t *PR = wpat + WP;
-    uint32_t *win = PR + ((KW + 3) & ~3u);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-
-    build_wheel_pattern<WHEEL, NT>(wpat);
-    for (uint32_t i = threadIdx.x; i < KW; i += NT) PR[i] = t.PR[i];
-
-    const uint32_t rbits = prm.rec_bits < prm.tile_bits ? prm.rec_bits : prm.tile_bits;
-    const bool whole = prm.tile_bits >= prm.rec_bits;
-    const unsigned long long rmask = (1ull << prm.rec_bits) - 1ull;
-
-    for (;;) {
-        if (threadIdx.x == 0) s.tile = prm.tile0 + atomicAdd(&ctrl->tile_ctr, 1ull);
-        __syncthreads();
-        const unsigned long long tile = s.tile;
-        if (tile >= prm.tile_end) break;
-        const unsigned long long k0 = tile << prm.tile_bits;
-        const unsigned long long left = prm.n_total - k0;
-        const uint32_t cnt = left < (1ull << prm.tile_bits) ? (uint32_t)left : (1u << prm.tile_bits);
-        const unsigned long long n_lo = prm.n0 + 2ull * k0;
-        const WinGeom g = tile_geom(n_lo, cnt, 32u * KW);
-        unsigned long long b0 = 0, b1 = 0;
-        if (prm.bk_ent) {
-            b0 = prm.bk_off[tile - prm.tile0];
-            b1 = prm.bk_off[tile - prm.tile0 + 1];
-        }
-        build_window<WHEEL, NT>(win, wpat, g, t, prm.bk_prime0, prm.bk_ent, b0, b1, ctrl);
-
-        for (uint32_t ks = 0; ks < cnt; ks += (1u << rbits)) {
-            const uint32_t ke = (cnt - ks) < (1u << rbits) ? cnt : ks + (1u << rbits);
-            const unsigned long long kg = k0 + ks;
-            DevRec *rec = &recs[kg >> prm.rec_bits];
-            const unsigned long long kr0 = kg & rmask;
-            LaneAcc a;
-            a.reset();
-            if (threadIdx.x < HIST_BINS) s.hist[threadIdx.x] = 0u;
-            __syncthreads();
-            for (uint32_t g32 = (ks >> 5) + warp; (g32 << 5) < ke; g32 += NWARP) {
-                const uint32_t k = (g32 << 5) + lane;
-                const bool valid = k < ke;
-                const unsigned long long n = n_lo + 2ull * k;
-                uint32_t pm = fast_pmin(win, PR, KW, g32, valid && n != 4ull);
-                if (valid && n == 4ull) pm = 2u;
-                uint32_t pend = __ballot_sync(GB_FULL_MASK, valid && pm == 0u);
-                while (pend) {
-                    const int src = __ffs(pend) - 1;
-                    pend &= pend - 1;
-                    const unsigned long long ns = __shfl_sync(GB_FULL_MASK, n, src);
-                    unsigned long long ps = slow_pmin(ns, prm.p_slow_start, prm.slow_cap_log2, ctrl);
-                    if (ps >= PMIN_LIMIT) {
-                        if (lane == 0) atomicOr(&ctrl->flags, F_OVERFLOW);
-                        ps = PMIN_LIMIT - 1;
-                    }
-                    if (lane == src) {
-                        pm = (uint32_t)ps;
-                        if (!ps) a.ce = a.ce > ~ns ? a.ce : ~ns;
-                    }
-                }
-                if (valid && pm) a.add(pm, kr0 + (k - ks), prm.p_max, s.hist);
-            }
-            reduce_to_record<NT>(a, s, rec, ke - ks, whole, ctrl);
-        }
-    }
-}
 
 // Zero the control block and (when tiles share records) the records.
 __global__ void clear_kernel(const RangeParams *__restrict__ prm_g, DevRec *recs, Ctrl *ctrl,
@@ -321,6 +144,8 @@ merge_kernel(const RangeParams *__restrict__ prm_g, const DevRec *__restrict__ r
         else if ((f & F_COUNTEREX) || cen) st = GB_COUNTEREXAMPLE;
         out->status = st;
         out->reserved = 0;
+        out->submit_ns = 0;
+        out->done_ns = 0;
     }
     if (threadIdx.x < 64) {
         unsigned long long h = 0;
@@ -676,22 +501,31 @@ cudaError_t launch_set_params(cudaStream_t st, RangeParams *dst, const RangePara
 }
 
 template <int WHEEL, int NT>
-static const void *persistent_ptr() { return (const void *)persistent_kernel<WHEEL, NT>; }
-template <int WHEEL, int NT>
 static const void *slice_ptr() { return (const void *)slice_sieve_kernel<WHEEL, NT>; }
 
-const void *persistent_kernel_ptr(int wheel, int nt)
+const void *persistent_kernel_ptr(int wheel, int nt, int bc)
 {
-    if (wheel == 13) {
-        if (nt == 256) return persistent_ptr<13, 256>();
-        if (nt == 512) return persistent_ptr<13, 512>();
-        if (nt == 1024) return persistent_ptr<13, 1024>();
-    } else if (wheel == 7) {
-        if (nt == 256) return persistent_ptr<7, 256>();
-        if (nt == 512) return persistent_ptr<7, 512>();
-        if (nt == 1024) return persistent_ptr<7, 1024>();
-    }
+    if (nt == 256) return persistent_ptr_256(wheel, bc);
+    if (nt == 512) return persistent_ptr_512(wheel, bc);
+    if (nt == 1024) return persistent_ptr_1024(wheel, bc);
     return nullptr;
+}
+
+const void *serve_kernel_ptr(int wheel, int nt, int bc)
+{
+    if (nt == 512) return serve_ptr_512(wheel, bc);
+    if (nt == 1024) return serve_ptr_1024(wheel, bc);
+    return nullptr;
+}
+
+cudaError_t launch_serve(const void *fn, int nt, int grid, size_t smem, cudaStream_t st,
+                         const unsigned long long *items, unsigned long long n_items, SlotDev *slots,
+                         const Tables &t, Ctrl *ctrl)
+{
+    if (!fn) return cudaErrorInvalidValue;
+    Tables tt = t;
+    void *args[] = {(void *)&items, (void *)&n_items, (void *)&slots, (void *)&tt, (void *)&ctrl};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(nt), args, smem, st);
 }
 
 const void *slice_kernel_ptr(int wheel, int nt)
@@ -714,10 +548,10 @@ uint32_t wheel_pattern_words(int wheel)
                        : (((WheelM<7>::M + 64 + 31) / 32 + 3) & ~3u);
 }
 
-cudaError_t launch_persistent(int wheel, int nt, int grid, size_t smem, cudaStream_t st,
+cudaError_t launch_persistent(int wheel, int nt, int bc, int grid, size_t smem, cudaStream_t st,
                               const RangeParams *prm, const Tables &t, DevRec *recs, Ctrl *ctrl)
 {
-    const void *fn = persistent_kernel_ptr(wheel, nt);
+    const void *fn = persistent_kernel_ptr(wheel, nt, bc);
     if (!fn) return cudaErrorInvalidValue;
     Tables tt = t;
     void *args[] = {(void *)&prm, (void *)&tt, (void *)&recs, (void *)&ctrl};

@@ -8,13 +8,25 @@
 
 namespace gbk {
 
-const void *persistent_kernel_ptr(int wheel, int nt);
+// bc: 0 = per-n search, 2..4 = bit-parallel search over p < 64 bc (wheel 7: bc 0 or 3)
+const void *persistent_kernel_ptr(int wheel, int nt, int bc);
+// defined in gb_persist_<NT>.cu
+const void *persistent_ptr_256(int wheel, int bc);
+const void *persistent_ptr_512(int wheel, int bc);
+const void *persistent_ptr_1024(int wheel, int bc);
+const void *serve_ptr_512(int wheel, int bc);
+const void *serve_ptr_1024(int wheel, int bc);
+// serving work-list kernel; nullptr when (wheel, nt, bc) has no instantiation
+const void *serve_kernel_ptr(int wheel, int nt, int bc);
+cudaError_t launch_serve(const void *fn, int nt, int grid, size_t smem, cudaStream_t st,
+                         const unsigned long long *items, unsigned long long n_items, SlotDev *slots,
+                         const Tables &t, Ctrl *ctrl);
 const void *slice_kernel_ptr(int wheel, int nt);
 uint32_t wheel_pattern_words(int wheel);
 size_t merge_part_bytes();
 uint32_t table_blocks(uint32_t nwords);
 
-cudaError_t launch_persistent(int wheel, int nt, int grid, size_t smem, cudaStream_t st,
+cudaError_t launch_persistent(int wheel, int nt, int bc, int grid, size_t smem, cudaStream_t st,
                               const RangeParams *prm, const Tables &t, DevRec *recs, Ctrl *ctrl);
 cudaError_t launch_clear(cudaStream_t st, const RangeParams *prm, DevRec *recs, Ctrl *ctrl,
                          int clear_records, int grid);

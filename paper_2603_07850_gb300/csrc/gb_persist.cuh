@@ -1,0 +1,268 @@
+// gb_persist.cuh -- the persistent fused kernel and the record reduction it
+// shares with the plain form.  Instantiated per thread count in
+// gb_persist_<NT>.cu so the variants compile in parallel.
+#pragma once
+#include <stdint.h>
+#include <cuda_runtime.h>
+
+#include "gb_device.cuh"
+#include "gb_search.cuh"
+
+namespace gbk {
+
+// ---------------------------------------------------------------------------
+// persistent fused kernel
+// ---------------------------------------------------------------------------
+
+struct RedScratch {
+    unsigned long long arg[32], sum[32], wsum[32], ce[32];
+    uint32_t mx[32], slow[32];
+    uint32_t hist[HIST_BINS];
+    unsigned long long tile;
+};
+
+// Fold one p_min into a lane's running record state.
+struct LaneAcc {
+    uint32_t mx, slow;
+    unsigned long long arg, sum, wsum, ce, hA, hB;
+    __device__ __forceinline__ void reset()
+    {
+        mx = 0; slow = 0; arg = ~0ull; sum = 0; wsum = 0; ce = 0; hA = 0; hB = 0;
+    }
+    __device__ __forceinline__ void add(uint32_t pm, unsigned long long kr, uint32_t p_max,
+                                        uint32_t *s_hist)
+    {
+        if (pm > mx) { mx = pm; arg = kr; }           // k ascends per lane: first max wins
+        sum += pm;
+        wsum += (unsigned long long)pm * (kr + 1ull);
+        slow += pm > p_max ? 1u : 0u;
+        uint32_t b = 31u - __clz(pm);                 // floor(log2 p_min) >= 1
+        if (b <= 4) hA += 1ull << (16u * (b - 1u));
+        else if (b <= 8) hB += 1ull << (16u * (b - 5u));
+        else atomicAdd(&s_hist[b], 1u);
+    }
+};
+
+// CTA-wide reduction of the lanes' state into record r.  `whole` = the tile
+// owns the record (plain stores) instead of sharing it (atomics).
+template <int NT>
+__device__ __forceinline__ void reduce_to_record(LaneAcc &a, RedScratch &s, DevRec *rec,
+                                                 uint32_t n_cnt, bool whole, Ctrl *ctrl)
+{
+    constexpr int NWARP = NT / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t wmax = __reduce_max_sync(GB_FULL_MASK, a.mx);
+    unsigned long long warg = warp_min_u64(a.mx == wmax ? a.arg : ~0ull);
+    unsigned long long wsum = warp_sum_u64(a.sum), wws = warp_sum_u64(a.wsum);
+    unsigned long long wce = a.ce;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long v = __shfl_xor_sync(GB_FULL_MASK, wce, o);
+        wce = v > wce ? v : wce;
+    }
+    uint32_t wslow = __reduce_add_sync(GB_FULL_MASK, a.slow);
+#pragma unroll
+    for (int f = 0; f < 4; f++) {
+        uint32_t ca = __reduce_add_sync(GB_FULL_MASK, (uint32_t)(a.hA >> (16 * f)) & 0xffffu);
+        uint32_t cb = __reduce_add_sync(GB_FULL_MASK, (uint32_t)(a.hB >> (16 * f)) & 0xffffu);
+        if (lane == 0) {
+            if (ca) atomicAdd(&s.hist[1 + f], ca);
+            if (cb) atomicAdd(&s.hist[5 + f], cb);
+        }
+    }
+    if (lane == 0) {
+        s.mx[warp] = wmax; s.arg[warp] = warg; s.sum[warp] = wsum; s.wsum[warp] = wws;
+        s.slow[warp] = wslow; s.ce[warp] = wce;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t m = lane < NWARP ? s.mx[lane] : 0u;
+        unsigned long long ar = lane < NWARP ? s.arg[lane] : ~0ull;
+        uint32_t cm = __reduce_max_sync(GB_FULL_MASK, m);
+        unsigned long long ca = warp_min_u64(m == cm ? ar : ~0ull);
+        unsigned long long su = warp_sum_u64(lane < NWARP ? s.sum[lane] : 0ull);
+        unsigned long long ws = warp_sum_u64(lane < NWARP ? s.wsum[lane] : 0ull);
+        uint32_t sl = __reduce_add_sync(GB_FULL_MASK, lane < NWARP ? s.slow[lane] : 0u);
+        unsigned long long ce = lane < NWARP ? s.ce[lane] : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            unsigned long long v = __shfl_xor_sync(GB_FULL_MASK, ce, o);
+            ce = v > ce ? v : ce;
+        }
+        unsigned long long key = cm ? (((unsigned long long)cm << KEY_SHIFT) | (KEY_KMASK - ca)) : 0ull;
+        if (whole) {
+            if (lane == 0) {
+                rec->key = key; rec->sum = su; rec->wsum = ws; rec->n_count = n_cnt;
+                rec->n_slow = sl; rec->ce_inv = ce;
+            }
+            rec->hist[lane] = s.hist[lane];
+        } else {
+            if (lane == 0) {
+                if (key) atomicMax(&rec->key, key);
+                atomicAdd(&rec->sum, su);
+                atomicAdd(&rec->wsum, ws);
+                atomicAdd(&rec->n_count, (unsigned long long)n_cnt);
+                if (sl) atomicAdd(&rec->n_slow, (unsigned long long)sl);
+                if (ce) atomicMax(&rec->ce_inv, ce);
+            }
+            if (s.hist[lane]) atomicAdd(&rec->hist[lane], (unsigned long long)s.hist[lane]);
+        }
+        if (lane == 0 && sl) atomicAdd(&ctrl->slow_total, (unsigned long long)sl);
+    }
+}
+
+// One tile: build its window, search every n, reduce into its record(s).
+// Called by every thread of the CTA (it contains barriers).
+template <int WHEEL, int NT, int SEARCH_BC>
+__device__ __forceinline__ void run_tile(const RangeParams &prm, unsigned long long tile, const Tables &t,
+                                         const uint32_t *wpat, const uint32_t *PR, uint32_t *win,
+                                         RedScratch &s, DevRec *recs, Ctrl *ctrl)
+{
+    constexpr int NWARP = NT / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t KW = prm.k_words;
+    const uint32_t rbits = prm.rec_bits < prm.tile_bits ? prm.rec_bits : prm.tile_bits;
+    const bool whole = prm.tile_bits >= prm.rec_bits;
+    const unsigned long long rmask = (1ull << prm.rec_bits) - 1ull;
+    // bit-parallel phase bound: candidates p <= bb (never above P_max or the
+    // search bound); the per-n phase starts at candidate index i_start
+    const uint32_t ps_odd = (uint32_t)(prm.p_slow_start - 2ull);
+    uint32_t bb = SEARCH_BC ? 64u * SEARCH_BC - 1u : 0u;
+    if (bb > ps_odd) bb = ps_odd;
+    if (bb > prm.p_max) bb = prm.p_max;
+    const uint32_t i_start = (bb + 1u) >> 1;
+    const unsigned long long k0 = tile << prm.tile_bits;
+    const unsigned long long left = prm.n_total - k0;
+    const uint32_t cnt = left < (1ull << prm.tile_bits) ? (uint32_t)left : (1u << prm.tile_bits);
+    const unsigned long long n_lo = prm.n0 + 2ull * k0;
+    const WinGeom g = tile_geom(n_lo, cnt, 32u * KW);
+    unsigned long long b0 = 0, b1 = 0;
+    if (prm.bk_ent) {
+        b0 = prm.bk_off[tile - prm.tile0];
+        b1 = prm.bk_off[tile - prm.tile0 + 1];
+    }
+    build_window<WHEEL, NT>(win, wpat, g, t, prm.bk_prime0, prm.bk_ent, b0, b1, ctrl);
+
+    for (uint32_t ks = 0; ks < cnt; ks += (1u << rbits)) {
+        const uint32_t ke = (cnt - ks) < (1u << rbits) ? cnt : ks + (1u << rbits);
+        const unsigned long long kg = k0 + ks;
+        DevRec *rec = &recs[kg >> prm.rec_bits];
+        const unsigned long long kr0 = kg & rmask;
+        LaneAcc a;
+        a.reset();
+        if (threadIdx.x < HIST_BINS) s.hist[threadIdx.x] = 0u;
+        __syncthreads();
+        if (SEARCH_BC == 0) {
+            for (uint32_t g32 = (ks >> 5) + warp; (g32 << 5) < ke; g32 += NWARP) {
+                const uint32_t k = (g32 << 5) + lane;
+                const bool valid = k < ke;
+                const unsigned long long n = n_lo + 2ull * k;
+                uint32_t pm = fast_pmin(win, PR, KW, g32, valid && n != 4ull);
+                if (valid && n == 4ull) pm = 2u;
+                uint32_t pend = __ballot_sync(GB_FULL_MASK, valid && pm == 0u);
+                while (pend) {
+                    const int src = __ffs(pend) - 1;
+                    pend &= pend - 1;
+                    const unsigned long long ns = __shfl_sync(GB_FULL_MASK, n, src);
+                    unsigned long long ps = slow_pmin(ns, prm.p_slow_start, prm.slow_cap_log2, ctrl);
+                    if (ps >= PMIN_LIMIT) {
+                        if (lane == 0) atomicOr(&ctrl->flags, F_OVERFLOW);
+                        ps = PMIN_LIMIT - 1;
+                    }
+                    if (lane == src) {
+                        pm = (uint32_t)ps;
+                        if (!ps) a.ce = a.ce > ~ns ? a.ce : ~ns;
+                    }
+                }
+                if (valid && pm) a.add(pm, kr0 + (k - ks), prm.p_max, s.hist);
+            }
+        } else {
+            SubAcc acc;
+            acc.reset();
+            const uint32_t wbeg = ks >> 5, wend = (ke + 31) >> 5;
+            for (uint32_t wb = wbeg + 32u * warp; wb < wend; wb += 32u * NWARP) {
+                const uint32_t w = wb + lane;
+                const bool inw = w < wend;
+                uint32_t valid = 0u;
+                if (inw) {
+                    const uint32_t kw0 = 32u * w;
+                    valid = (kw0 + 32u <= ke) ? 0xffffffffu : (0xffffffffu >> (32u - (ke - kw0)));
+                }
+                const uint32_t wl = w - wbeg;
+                const uint32_t U = bulk_word<SEARCH_BC>(win, inw ? w : wend - 1u, wl, KW, valid, bb,
+                                                        prm.p_max, acc, s.hist);
+                tail_words(win, PR, KW, U, wl, n_lo, ks, i_start, prm, acc, s.hist, ctrl);
+            }
+            a.mx = acc.mx;
+            a.arg = acc.mx ? kr0 + acc.arg : ~0ull;
+            a.sum = acc.sum;
+            a.wsum = acc.wsum + kr0 * acc.sum;
+            a.slow = acc.slow;
+            a.ce = acc.ce;
+            a.hA = (unsigned long long)acc.h[1] | ((unsigned long long)acc.h[2] << 16) |
+                   ((unsigned long long)acc.h[3] << 32) | ((unsigned long long)acc.h[4] << 48);
+            a.hB = (unsigned long long)acc.h[5] | ((unsigned long long)acc.h[6] << 16) |
+                   ((unsigned long long)acc.h[7] << 32) | ((unsigned long long)acc.h[8] << 48);
+        }
+        reduce_to_record<NT>(a, s, rec, ke - ks, whole, ctrl);
+    }
+}
+
+// SEARCH_BC = 0: per-n search (one lane per n, 32 candidates per step).
+// SEARCH_BC = 2..4: bit-parallel search of the candidates p < 64 SEARCH_BC
+// (one lane per 32 n), the rest per n after warp compaction.
+template <int WHEEL, int NT, int SEARCH_BC>
+__global__ void __launch_bounds__(NT, 1)
+persistent_kernel(const RangeParams *__restrict__ prm_g, Tables t, DevRec *__restrict__ recs,
+                  Ctrl *ctrl)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ RedScratch s;
+    constexpr uint32_t WP = ((WheelM<WHEEL>::M + 64 + 31) / 32 + 3) & ~3u;
+    const RangeParams prm = *prm_g;
+    const uint32_t KW = prm.k_words;
+    uint32_t *wpat = smem;
+    uint32_t *PR = wpat + WP;
+    uint32_t *win = PR + ((KW + 3) & ~3u);
+    build_wheel_pattern<WHEEL, NT>(wpat);
+    for (uint32_t i = threadIdx.x; i < KW; i += NT) PR[i] = t.PR[i];
+    for (;;) {
+        if (threadIdx.x == 0) s.tile = prm.tile0 + atomicAdd(&ctrl->tile_ctr, 1ull);
+        __syncthreads();
+        const unsigned long long tile = s.tile;
+        if (tile >= prm.tile_end) break;
+        run_tile<WHEEL, NT, SEARCH_BC>(prm, tile, t, wpat, PR, win, s, recs, ctrl);
+    }
+}
+
+// Serving: CTAs claim work items (slot, tile) of the admitted requests from a
+// device counter, so the tiles of many requests share one persistent launch;
+// each tile folds into its request's record with atomics.
+template <int WHEEL, int NT, int SEARCH_BC>
+__global__ void __launch_bounds__(NT, 1)
+serve_kernel(const unsigned long long *__restrict__ items, unsigned long long n_items, SlotDev *slots,
+             Tables t, Ctrl *ctrl)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ RedScratch s;
+    constexpr uint32_t WP = ((WheelM<WHEEL>::M + 64 + 31) / 32 + 3) & ~3u;
+    const uint32_t KW = t.k_words;
+    uint32_t *wpat = smem;
+    uint32_t *PR = wpat + WP;
+    uint32_t *win = PR + ((KW + 3) & ~3u);
+    build_wheel_pattern<WHEEL, NT>(wpat);
+    for (uint32_t i = threadIdx.x; i < KW; i += NT) PR[i] = t.PR[i];
+    for (;;) {
+        if (threadIdx.x == 0) s.tile = atomicAdd(&ctrl->work_ctr, 1ull);
+        __syncthreads();
+        const unsigned long long idx = s.tile;
+        if (idx >= n_items) break;
+        const unsigned long long item = items[idx];
+        const unsigned long long slot = item >> SERVE_SLOT_SHIFT;
+        const unsigned long long tile = item & ((1ull << SERVE_SLOT_SHIFT) - 1ull);
+        const RangeParams prm = slots[slot].prm;
+        run_tile<WHEEL, NT, SEARCH_BC>(prm, tile, t, wpat, PR, win, s, &slots[slot].acc, ctrl);
+    }
+}
+
+}  // namespace gbk

@@ -1,0 +1,33 @@
+// gb_persist_1024.cu -- persistent_kernel instantiations with 1024 threads per CTA.
+#include "gb_kernels.h"
+#include "gb_persist.cuh"
+
+namespace gbk {
+
+const void *persistent_ptr_1024(int wheel, int bc)
+{
+    if (wheel == 13) {
+        switch (bc) {
+            case 0: return (const void *)persistent_kernel<13, 1024, 0>;
+            case 2: return (const void *)persistent_kernel<13, 1024, 2>;
+            case 3: return (const void *)persistent_kernel<13, 1024, 3>;
+            case 4: return (const void *)persistent_kernel<13, 1024, 4>;
+        }
+    } else if (wheel == 7) {
+        switch (bc) {
+            case 0: return (const void *)persistent_kernel<7, 1024, 0>;
+            case 3: return (const void *)persistent_kernel<7, 1024, 3>;
+            case 4: return (const void *)persistent_kernel<7, 1024, 4>;
+        }
+    }
+    return nullptr;
+}
+
+const void *serve_ptr_1024(int wheel, int bc)
+{
+    if (wheel == 13 && bc == 3) return (const void *)serve_kernel<13, 1024, 3>;
+    if (wheel == 13 && bc == 0) return (const void *)serve_kernel<13, 1024, 0>;
+    return nullptr;
+}
+
+}  // namespace gbk

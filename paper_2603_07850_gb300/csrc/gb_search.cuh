@@ -1,0 +1,261 @@
+// gb_search.cuh -- bit-parallel p_min search over one tile window.
+//
+// For the 32 consecutive even n of one word w (n index k = 32w + b), the
+// candidate p = 2i + 1 maps to window bit k + K - 1 - i, so the 32 lookups of
+// one candidate for the whole word are one funnel shift of two window words
+// by the constant 31 - (i mod 32) (paper Sec. 5.3: bitwise bulk marking,
+// 32 n per instruction).  A lane owns one word and walks the odd primes
+// p < 64 BC in ascending order (compile-time unrolled); each candidate
+// resolves the bits that are still open:
+//     x  = funnelshift(window words);  nw = x & ~V;  V |= x;
+// and records p in bit-sliced form (plane j gets nw when bit j of p is 1).
+// The record statistics of the word then come from the planes with popcounts:
+// sum, wsum, the log2 histogram and the max with its smallest n.  The few n
+// left open (p_min >= 64 BC) are compacted across the warp and finish with
+// the per-n search from chunk BC on, then the exact slow path.
+#pragma once
+#include "gb_device.cuh"
+
+namespace gbk {
+
+constexpr int CAND_COUNT = 53;              // odd primes below 256
+
+__host__ __device__ constexpr uint32_t cand_prime(int i)
+{
+    switch (i) {
+        case 0: return 3u;
+        case 1: return 5u;
+        case 2: return 7u;
+        case 3: return 11u;
+        case 4: return 13u;
+        case 5: return 17u;
+        case 6: return 19u;
+        case 7: return 23u;
+        case 8: return 29u;
+        case 9: return 31u;
+        case 10: return 37u;
+        case 11: return 41u;
+        case 12: return 43u;
+        case 13: return 47u;
+        case 14: return 53u;
+        case 15: return 59u;
+        case 16: return 61u;
+        case 17: return 67u;
+        case 18: return 71u;
+        case 19: return 73u;
+        case 20: return 79u;
+        case 21: return 83u;
+        case 22: return 89u;
+        case 23: return 97u;
+        case 24: return 101u;
+        case 25: return 103u;
+        case 26: return 107u;
+        case 27: return 109u;
+        case 28: return 113u;
+        case 29: return 127u;
+        case 30: return 131u;
+        case 31: return 137u;
+        case 32: return 139u;
+        case 33: return 149u;
+        case 34: return 151u;
+        case 35: return 157u;
+        case 36: return 163u;
+        case 37: return 167u;
+        case 38: return 173u;
+        case 39: return 179u;
+        case 40: return 181u;
+        case 41: return 191u;
+        case 42: return 193u;
+        case 43: return 197u;
+        case 44: return 199u;
+        case 45: return 211u;
+        case 46: return 223u;
+        case 47: return 227u;
+        case 48: return 229u;
+        case 49: return 233u;
+        case 50: return 239u;
+        case 51: return 241u;
+        case 52: return 251u;
+        default: return 0u;
+    }
+}
+
+// Number of candidates below 64 * bc (bc = 1..4): 17, 30, 42, 53.
+__host__ __device__ constexpr int cand_count(int bc)
+{
+    return bc == 1 ? 17 : bc == 2 ? 30 : bc == 3 ? 42 : 53;
+}
+
+// sum over the set bits b of x of b
+__device__ __forceinline__ uint32_t bitpos_sum(uint32_t x)
+{
+    return __popc(x & 0xAAAAAAAAu) + 2u * __popc(x & 0xCCCCCCCCu) + 4u * __popc(x & 0xF0F0F0F0u) +
+           8u * __popc(x & 0xFF00FF00u) + 16u * __popc(x & 0xFFFF0000u);
+}
+
+// Per-lane running state of one sub-record: sums relative to the sub-record
+// start (k_rel = k - ks), converted to record-relative values at the end.
+struct SubAcc {
+    uint32_t mx, arg, slow;                 // max p_min, its k_rel, #(p_min > P_max)
+    unsigned long long sum, wsum, ce;       // sum p, sum p * (k_rel + 1), ~n of a counterexample
+    uint32_t h[9];                          // counts of bins 1..8 (index 0 unused)
+    __device__ __forceinline__ void reset()
+    {
+        mx = 0; arg = 0xffffffffu; slow = 0; sum = 0; wsum = 0; ce = 0;
+#pragma unroll
+        for (int b = 0; b < 9; b++) h[b] = 0;
+    }
+    __device__ __forceinline__ void take_max(uint32_t p, uint32_t k)
+    {
+        if (p > mx || (p == mx && k < arg)) { mx = p; arg = k; }
+    }
+};
+
+// One word of the bulk phase: resolves candidates p < 64 BC with p <= bb,
+// folds the resolved bits into acc and returns the still-open bits.  bb never
+// exceeds P_max, so nothing resolved here counts towards n_slow.
+template <int BC>
+__device__ __forceinline__ uint32_t bulk_word(const uint32_t *win, uint32_t w, uint32_t wl, uint32_t KW,
+                                              uint32_t valid, uint32_t bb, uint32_t p_max, SubAcc &acc,
+                                              uint32_t *s_hist)
+{
+    uint32_t V = ~valid;
+    uint32_t B0 = 0, B1 = 0, B2 = 0, B3 = 0, B4 = 0, B5 = 0, B6 = 0, B7 = 0;
+#pragma unroll
+    for (int c = 0; c < BC; c++) {
+        const uint32_t lo = win[w + KW - 1 - c], hi = win[w + KW - c];
+#pragma unroll
+        for (int ci = 0; ci < cand_count(BC); ci++) {
+            const uint32_t p = cand_prime(ci);
+            const uint32_t i = (p - 1) >> 1;
+            if ((int)(i >> 5) == c && p <= bb) {
+                const uint32_t x = __funnelshift_r(lo, hi, 31u - (i & 31u));
+                const uint32_t nw = x & ~V;
+                V |= x;
+                if (p & 1u) B0 |= nw;
+                if (p & 2u) B1 |= nw;
+                if (p & 4u) B2 |= nw;
+                if (p & 8u) B3 |= nw;
+                if (p & 16u) B4 |= nw;
+                if (p & 32u) B5 |= nw;
+                if (p & 64u) B6 |= nw;
+                if (p & 128u) B7 |= nw;
+            }
+        }
+    }
+    const uint32_t R = V & valid;                     // resolved n of this word
+    if (R) {
+        // sum and sum of b * p over the word, plane by plane
+        const uint32_t Bs[8] = {B0, B1, B2, B3, B4, B5, B6, B7};
+        uint32_t s = 0, sb = 0;
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            s += __popc(Bs[j]) << j;
+            sb += bitpos_sum(Bs[j]) << j;
+        }
+        acc.sum += s;
+        acc.wsum += (unsigned long long)s * (32ull * wl + 1ull) + sb;
+        // histogram: bin = index of the highest plane that is set
+        uint32_t H = 0;
+#pragma unroll
+        for (int j = 7; j >= 1; j--) {
+            acc.h[j] += __popc(Bs[j] & ~H);
+            H |= Bs[j];
+        }
+        // max over the word and its smallest n
+        uint32_t cand = R, mx = 0;
+#pragma unroll
+        for (int j = 7; j >= 0; j--) {
+            const uint32_t t = cand & Bs[j];
+            if (t) { cand = t; mx |= 1u << j; }
+        }
+        acc.take_max(mx, 32u * wl + (uint32_t)(__ffs(cand) - 1));
+    }
+    (void)s_hist;
+    return valid & ~V;
+}
+
+// The open n of a warp's 32 words: compacted 32 at a time across the warp,
+// searched per n from candidate index i_start on, slow path last.
+__device__ __forceinline__ void tail_words(const uint32_t *win, const uint32_t *PR, uint32_t KW,
+                                           uint32_t U, uint32_t wl, unsigned long long n_lo,
+                                           uint32_t ks, uint32_t i_start, const RangeParams &prm,
+                                           SubAcc &acc, uint32_t *s_hist, Ctrl *ctrl)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t cnt = __popc(U);
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(GB_FULL_MASK, incl, o);
+        if (lane >= (uint32_t)o) incl += y;
+    }
+    const uint32_t total = __shfl_sync(GB_FULL_MASK, incl, 31);
+    const uint32_t excl = incl - cnt;
+    const uint32_t KB = 32u * KW;
+    const uint32_t t0 = i_start >> 5;
+    const uint32_t mask0 = 0xffffffffu >> (i_start & 31u);
+    for (uint32_t r = 0; r < total; r += 32) {
+        const uint32_t gi = r + lane;
+        const bool act = gi < total;
+        // owner lane: the number of lanes whose inclusive count is <= gi
+        uint32_t o = 0;
+#pragma unroll
+        for (uint32_t st = 16; st > 0; st >>= 1) {
+            const uint32_t v = __shfl_sync(GB_FULL_MASK, incl, (o + st - 1) & 31);
+            if (v <= gi) o += st;
+        }
+        o &= 31;
+        const uint32_t Uo = __shfl_sync(GB_FULL_MASK, U, o);
+        const uint32_t eo = __shfl_sync(GB_FULL_MASK, excl, o);
+        const uint32_t wlo = __shfl_sync(GB_FULL_MASK, wl, o);
+        const uint32_t b = act ? __fns(Uo, 0, (int)(gi - eo) + 1) : 0u;
+        const uint32_t kr = 32u * wlo + b;            // k relative to ks
+        const uint32_t k = ks + kr;                   // k within the tile
+        const unsigned long long n = n_lo + 2ull * k;
+        uint32_t pm = 0;
+        if (act) {
+            if (n == 4ull) {
+                pm = 2u;
+            } else {
+                for (uint32_t t = t0; t < KW; ++t) {
+                    const uint32_t s = k + KB - 32u - 32u * t;
+                    const uint32_t x = __funnelshift_r(win[s >> 5], win[(s >> 5) + 1], s & 31u);
+                    uint32_t m = x & PR[t];
+                    if (t == t0) m &= mask0;
+                    if (m) { pm = 2u * (32u * t + __clz(m)) + 1u; break; }
+                }
+            }
+        }
+        uint32_t pend = __ballot_sync(GB_FULL_MASK, act && pm == 0u);
+        while (pend) {
+            const int src = __ffs(pend) - 1;
+            pend &= pend - 1;
+            const unsigned long long ns = __shfl_sync(GB_FULL_MASK, n, src);
+            unsigned long long ps = slow_pmin(ns, prm.p_slow_start, prm.slow_cap_log2, ctrl);
+            if (ps >= PMIN_LIMIT) {
+                if (lane == 0) atomicOr(&ctrl->flags, F_OVERFLOW);
+                ps = PMIN_LIMIT - 1;
+            }
+            if ((int)lane == src) {
+                pm = (uint32_t)ps;
+                if (!ps) acc.ce = acc.ce > ~ns ? acc.ce : ~ns;
+            }
+        }
+        if (act && pm) {
+            acc.take_max(pm, kr);
+            acc.sum += pm;
+            acc.wsum += (unsigned long long)pm * (kr + 1ull);
+            acc.slow += pm > prm.p_max ? 1u : 0u;
+            const uint32_t bin = 31u - __clz(pm);
+            if (bin <= 8) {
+#pragma unroll
+                for (uint32_t hb = 1; hb <= 8; hb++) acc.h[hb] += bin == hb ? 1u : 0u;
+            } else {
+                atomicAdd(&s_hist[bin], 1u);
+            }
+        }
+    }
+}
+
+}  // namespace gbk

@@ -57,6 +57,14 @@ struct __align__(16) RangeParams {
     const uint32_t *bk_ent;            // window bit indices; nullptr = no buckets
 };
 
+// Serving: one admitted request.  Its params have rec_bits = 40 so the whole
+// request folds into the single record acc (requests have fewer than 2^40 n).
+struct __align__(16) SlotDev {
+    RangeParams prm;
+    DevRec acc;
+};
+constexpr int SERVE_SLOT_SHIFT = 40;       // work item = (slot << 40) | tile
+
 // Read-only device tables shared by every kernel.
 struct Tables {
     const uint32_t *primes;            // odd primes ascending, primes[0] = 3
