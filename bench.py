@@ -343,9 +343,13 @@ def run_ours(args):
         plain = {"value": pr["n_count"] / plain_s, "unit": "even_n/s", "seconds": plain_s,
                  "seg_bits": gb.gb_get_option("plain_seg_bits")}
 
-    # max over ranks of the step time and of the e2e time
+    # max over ranks of the step time and of the e2e time; the results of the
+    # ranks' blocks merge into one (the only exchange)
     tot_n = out["n_count"]
+    merged = out
     if dist:
+        from paper_2603_07850_gb300 import multi
+        merged = multi.gather_merge(out)
         t = torch.tensor([ms, e2e_s, float(out["n_count"])], dtype=torch.float64, device="cuda")
         g = [torch.zeros_like(t) for _ in range(world)]
         dist.all_gather(g, t)
@@ -393,7 +397,7 @@ def run_ours(args):
                                   "(derived, of measured clock)"},
         "plain": plain,
         "speedup_vs_plain": (tot_n / (ms * 1e-3)) / plain["value"] if plain else None,
-        "result": {k: out[k] for k in ("n_count", "max_pmin", "argmax_n", "sum_pmin", "n_slow")},
+        "result": {k: merged[k] for k in ("n_count", "max_pmin", "argmax_n", "sum_pmin", "n_slow")},
     }
     try:
         v, n, dt, k = cpu_sample(args.n_top, args.cpu_records)

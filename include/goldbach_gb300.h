@@ -121,7 +121,8 @@ typedef struct {
  *              size the kernels use).
  *
  * Builds the small-candidate table and the base primes <= 2^16 on the
- * device.  Calling gb_init again re-initialises (gb_shutdown first).
+ * device.  Calling gb_init again re-initialises (gb_shutdown first); every
+ * gb_init starts from the default options.
  * Returns GB_OK, GB_EINVAL, GB_ENOMEM or GB_ECUDA.
  */
 int gb_init(uint32_t p_max, uint32_t seg_bits);

@@ -143,15 +143,54 @@ int cuda_status(cudaError_t e, const char *what)
     return e == cudaErrorMemoryAllocation ? GB_ENOMEM : GB_ECUDA;
 }
 
+// Host-side fault injection for the failure-path tests: GB_FAULT="kind:k"
+// (kind = malloc, launch or memcpy) makes the k-th such call, counted from
+// gb_init, fail before it reaches CUDA.  No GPU fault is ever provoked.
+struct FaultShim {
+    int kind = -1;                    // 0 malloc, 1 launch, 2 memcpy
+    long long at = 0, seen[3] = {0, 0, 0};
+};
+FaultShim g_fault;
+
+void fault_configure()
+{
+    g_fault = FaultShim{};
+    const char *f = getenv("GB_FAULT");
+    if (!f) return;
+    static const char *names[3] = {"malloc:", "launch:", "memcpy:"};
+    for (int k = 0; k < 3; k++) {
+        size_t n = strlen(names[k]);
+        if (!strncmp(f, names[k], n)) { g_fault.kind = k; g_fault.at = atoll(f + n); }
+    }
+}
+
+// 0, or the status of an injected failure of this call
+int fault_pre(int kind, const char *what)
+{
+    if (g_fault.kind != kind) return GB_OK;
+    if (++g_fault.seen[kind] != g_fault.at) return GB_OK;
+    set_error("injected failure (GB_FAULT) at %s", what);
+    return kind == 0 ? GB_ENOMEM : GB_ECUDA;
+}
+
+int fault_kind_of(const char *what)
+{
+    if (strstr(what, "launch_")) return 1;
+    if (strstr(what, "cudaMemcpy")) return 2;
+    return -2;
+}
+
 #define CK(x)                                                   \
     do {                                                        \
-        int rc_ = cuda_status((x), #x);                         \
+        int rc_ = fault_pre(fault_kind_of(#x), #x);             \
+        if (rc_ == GB_OK) rc_ = cuda_status((x), #x);           \
         if (rc_ != GB_OK) return rc_;                           \
     } while (0)
 
 template <class T>
 int dev_alloc(T **p, size_t bytes)
 {
+    if (int frc = fault_pre(0, "cudaMalloc")) return frc;
     void *q = nullptr;
     cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
     if (e != cudaSuccess) {
@@ -885,6 +924,8 @@ int init_locked(uint32_t p_max, uint32_t seg_bits)
     if (p_max < 2 || p_max > (1u << 20)) { set_error("p_max must be in [2, 2^20]"); return GB_EINVAL; }
     if (seg_bits < 5 || seg_bits > 40) { set_error("seg_bits must be in [5, 40]"); return GB_EINVAL; }
     if (g.inited) release_all();
+    g.opt = Options{};               // a new context starts from the default options
+    fault_configure();
     CK(cudaGetDevice(&g.device));
     cudaDeviceProp prop;
     CK(cudaGetDeviceProperties(&prop, g.device));
@@ -1102,8 +1143,22 @@ int ctx_serve_launch(int buf, size_t n)
 
 // Wait for batch buf and read its status flags.  Touches only the serving
 // streams and buffers, so the caller does not hold the context lock.
-int ctx_serve_wait(int buf, unsigned int *flags)
+int ctx_serve_wait(int buf, unsigned int *flags, int64_t timeout_ms)
 {
+    if (timeout_ms >= 0) {
+        // bounded wait: poll the batch's event, give up after timeout_ms
+        const auto t0 = std::chrono::steady_clock::now();
+        for (;;) {
+            cudaError_t q = cudaEventQuery(sv.ev[buf]);
+            if (q == cudaSuccess) break;
+            if (q != cudaErrorNotReady) CK(q);
+            if (std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(timeout_ms)) {
+                set_error("serving batch did not finish within %lld ms", (long long)timeout_ms);
+                return GB_ETIMEOUT;
+            }
+            std::this_thread::sleep_for(std::chrono::microseconds(50));
+        }
+    }
     CK(cudaStreamWaitEvent(sv.cp, sv.ev[buf], 0));
     CK(cudaMemcpyAsync(sv.h_flags, &sv.d_ctrl->flags, 4, cudaMemcpyDeviceToHost, sv.cp));
     CK(cudaStreamSynchronize(sv.cp));

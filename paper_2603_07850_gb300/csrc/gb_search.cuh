@@ -119,8 +119,9 @@ __device__ __forceinline__ uint32_t bulk_word(const uint32_t *win, uint32_t w, u
                                               uint32_t valid, uint32_t bb, uint32_t p_max, SubAcc &acc,
                                               uint32_t *s_hist)
 {
-    uint32_t V = ~valid;
-    uint32_t B0 = 0, B1 = 0, B2 = 0, B3 = 0, B4 = 0, B5 = 0, B6 = 0, B7 = 0;
+    // Every candidate is odd, so plane 0 collects exactly the resolved bits:
+    // it doubles as the "already resolved" mask (invalid bits start set).
+    uint32_t B0 = ~valid, B1 = 0, B2 = 0, B3 = 0, B4 = 0, B5 = 0, B6 = 0, B7 = 0;
 #pragma unroll
     for (int c = 0; c < BC; c++) {
         const uint32_t lo = win[w + KW - 1 - c], hi = win[w + KW - c];
@@ -130,19 +131,20 @@ __device__ __forceinline__ uint32_t bulk_word(const uint32_t *win, uint32_t w, u
             const uint32_t i = (p - 1) >> 1;
             if ((int)(i >> 5) == c && p <= bb) {
                 const uint32_t x = __funnelshift_r(lo, hi, 31u - (i & 31u));
-                const uint32_t nw = x & ~V;
-                V |= x;
-                if (p & 1u) B0 |= nw;
-                if (p & 2u) B1 |= nw;
-                if (p & 4u) B2 |= nw;
-                if (p & 8u) B3 |= nw;
-                if (p & 16u) B4 |= nw;
-                if (p & 32u) B5 |= nw;
-                if (p & 64u) B6 |= nw;
-                if (p & 128u) B7 |= nw;
+                // plane j gets the newly resolved bits x & ~B0 (one 3-input op each)
+                if (p & 2u) B1 |= x & ~B0;
+                if (p & 4u) B2 |= x & ~B0;
+                if (p & 8u) B3 |= x & ~B0;
+                if (p & 16u) B4 |= x & ~B0;
+                if (p & 32u) B5 |= x & ~B0;
+                if (p & 64u) B6 |= x & ~B0;
+                if (p & 128u) B7 |= x & ~B0;
+                B0 |= x;
             }
         }
     }
+    const uint32_t V = B0;
+    B0 &= valid;
     const uint32_t R = V & valid;                     // resolved n of this word
     if (R) {
         // sum and sum of b * p over the word, plane by plane

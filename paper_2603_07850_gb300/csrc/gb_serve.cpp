@@ -114,9 +114,9 @@ void worker_loop()
             if (s.stop) break;
             // ---- admit ---------------------------------------------------------
             while (!s.pending.empty() && !s.free_slots.empty()) {
-                Req &r = s.reqs[s.pending.front()];
+                Req &r = s.reqs.at(s.pending.front());
                 uint64_t tb = 0;
-                for (uint64_t id : s.active) tb = std::max(tb, s.reqs[id].table_bytes);
+                for (uint64_t id : s.active) tb = std::max(tb, s.reqs.at(id).table_bytes);
                 tb = std::max(tb, r.table_bytes);
                 if (tb + (s.active.size() + 1) * slot_bytes > budget) break;   // wait for room
                 bool grow;
@@ -152,7 +152,7 @@ void worker_loop()
                 while (batch_items.size() < cap && any) {
                     any = false;
                     for (uint64_t id : s.active) {
-                        Req &r = s.reqs[id];
+                        Req &r = s.reqs.at(id);
                         if (r.next_tile >= r.sp.ntiles) continue;
                         items[batch_items.size()] =
                             ((unsigned long long)r.slot << SERVE_SLOT_SHIFT) | r.next_tile;
@@ -175,7 +175,7 @@ void worker_loop()
             if (rc != GB_OK) {
                 std::lock_guard<std::mutex> lk(s.mu);
                 for (uint64_t id : s.active) {
-                    Req &r = s.reqs[id];
+                    Req &r = s.reqs.at(id);
                     s.free_slots.push_back(r.slot);
                     finish(r, rc, nullptr);
                 }
@@ -192,15 +192,43 @@ void worker_loop()
             Batch b = inflight.front();
             inflight.pop_front();
             unsigned int flags = 0;
-            const int rc = ctx_serve_wait(b.buf, &flags);     // no context lock while waiting
+            // no context lock while waiting; bounded by the timeout_ms option
+            const int rc = ctx_serve_wait(b.buf, &flags, ctx_option("timeout_ms"));
+            if (rc == GB_ETIMEOUT) {
+                // report at once: every admitted and every pending request fails.
+                // Their slots are taken now: gb_poll may erase a finished request.
+                std::vector<int> held;
+                {
+                    std::lock_guard<std::mutex> lk(s.mu);
+                    for (uint64_t id : s.active) {
+                        Req &r = s.reqs.at(id);
+                        held.push_back(r.slot);
+                        r.slot = -1;
+                        finish(r, GB_ETIMEOUT, nullptr);
+                    }
+                    for (uint64_t id : s.pending) finish(s.reqs.at(id), GB_ETIMEOUT, nullptr);
+                    s.pending.clear();
+                    s.active.clear();
+                    s.cv_done.notify_all();
+                }
+                // then let the device finish before any slot or buffer is reused
+                unsigned int f;
+                ctx_serve_wait(b.buf, &f, -1);
+                for (auto &o : inflight) ctx_serve_wait(o.buf, &f, -1);
+                inflight.clear();
+                std::lock_guard<std::mutex> lk(s.mu);
+                for (int sl : held) s.free_slots.push_back(sl);
+                continue;
+            }
             std::vector<std::pair<uint64_t, gb_result>> out;
             for (uint64_t id : b.finishing) {
                 ServePlan sp;
                 int slot;
                 {
                     std::lock_guard<std::mutex> lk(s.mu);
-                    sp = s.reqs[id].sp;
-                    slot = s.reqs[id].slot;
+                    const Req &rq = s.reqs.at(id);      // unfinished: gb_poll cannot erase it
+                    sp = rq.sp;
+                    slot = rq.slot;
                 }
                 gb_result res{};
                 int frc = rc;
@@ -210,7 +238,7 @@ void worker_loop()
             }
             std::lock_guard<std::mutex> lk(s.mu);
             for (auto &pr : out) {
-                Req &r = s.reqs[pr.first];
+                Req &r = s.reqs.at(pr.first);
                 s.free_slots.push_back(r.slot);
                 r.slot = -1;
                 for (size_t i = 0; i < s.active.size(); i++)
@@ -224,7 +252,7 @@ void worker_loop()
     std::lock_guard<std::recursive_mutex> ck(ctx_mutex());
     for (auto &b : inflight) {
         unsigned int f;
-        ctx_serve_wait(b.buf, &f);
+        ctx_serve_wait(b.buf, &f, -1);
     }
 }
 

@@ -26,7 +26,8 @@ bool ctx_serve_needs_table(uint64_t lo, uint64_t hi);
 int ctx_serve_init_slot(int slot, const ServePlan &sp);
 unsigned long long *ctx_serve_items(int buf);
 int ctx_serve_launch(int buf, size_t n);
-int ctx_serve_wait(int buf, unsigned int *flags);
+// timeout_ms < 0: wait without bound
+int ctx_serve_wait(int buf, unsigned int *flags, int64_t timeout_ms);
 int ctx_serve_fetch(int slot, const ServePlan &sp, unsigned int flags, gb_result *out);
 size_t ctx_serve_slot_bytes();
 // provided by gb_serve.cpp
