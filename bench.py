@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--n-top", type=int, default=N_TOP)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--cpu-records", type=int, default=600)
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default configuration")
     return ap.parse_args()
 
 
@@ -277,7 +278,7 @@ def run_ours(args):
     gb.load()
     gb.gb_init(P_MAX, SEG_BITS)
     gb.gb_set_option("time_kernel", 1)
-    gb.gb_set_option("autotune", 1)          # the first warm-up step tunes
+    gb.gb_set_option("autotune", 0 if args.no_autotune else 1)   # the first warm-up step tunes
     lo = rank * args.n_top + 4
     hi = (rank + 1) * args.n_top + 1
     n_total = (hi - 1 - lo) // 2 + 1 if lo % 2 == 0 else None

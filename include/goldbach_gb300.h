@@ -140,16 +140,16 @@ int gb_init(uint32_t p_max, uint32_t seg_bits);
  *   "use_graph"     1 = replay a captured CUDA graph (default), 0 = direct launches
  *   "slow_cap"      log2 of the slow-path candidate cap per n, 6..24 (default 24)
  *   "timeout_ms"    bound for device-side waits and gb_poll defaults (default 600000)
- *   "tier_b_min"    smallest prime crossed off lane-per-prime (default 4096)
+ *   "tier_b_min"    smallest prime crossed off lane-per-prime (default 16384)
  *   "plain_slice_bits" log2 window bits per CTA in the plain sieve kernel (default 18)
  *   "time_kernel"   1 = time the persistent kernel with CUDA events (default 0)
- *   "search_chunks" bit-parallel search over the candidates p < 64 * this: 2, 3 or 4
- *                   (default 4); 0 = one lane per n (wheel 7 allows 0, 3, 4)
+ *   "search_chunks" bit-parallel search over the candidates p < 64 * this: 4, 6 or 8
+ *                   (default 4); 0 = one lane per n (wheel 7 allows 0, 4, 8)
  *   "serve_batch_tiles" tiles per serving launch (default 1024)
  *   "autotune"      1 = before the first call of each range class (GPU, P_max,
  *                   log2 of the largest n), time the kernel configurations on a
  *                   probe at the top of the range and keep the fastest (tile_bits,
- *                   threads, search_chunks, pattern_max, search_pmax); the choice
+ *                   threads, search_chunks, pattern_max, search_pmax, tier_b_min); the choice
  *                   is cached, and saved to the file named by GB_TUNE_CACHE if set.
  *                   The tuning call synchronises.  Results never depend on it.
  *   "search_pmax"   bound of the in-window candidate search, 0 = P_max (default 0);

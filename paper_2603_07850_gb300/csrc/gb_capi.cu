@@ -41,7 +41,7 @@ struct Options {
     int64_t ctas_per_sm = 0;       // 0 = as many as fit
     int64_t wheel = 13;
     int64_t pattern_max = 31;
-    int64_t tier_b_min = 4096;
+    int64_t tier_b_min = 16384;
     int64_t base_limit = 0;
     int64_t mem_budget_mb = 8192;
     int64_t plain_seg_bits = 26;
@@ -111,7 +111,7 @@ struct Ctx {
     size_t bk_ent_cap = 0;
     std::map<uint64_t, uint32_t> odd_primes_below;  // cache: bound -> #odd primes below it
     char dev_name[256] = {0};
-    struct TuneCfg { int64_t tile_bits, threads, search_chunks, pattern_max, search_pmax; };
+    struct TuneCfg { int64_t tile_bits, threads, search_chunks, pattern_max, search_pmax, tier_b_min; };
     std::map<std::string, TuneCfg> tuned;       // autotuner results by range class
     bool ev_pending = false;
 };
@@ -415,7 +415,7 @@ int occupancy_grid(const void *fn, int nt, size_t smem, int *grid)
 {
     if (!fn) {
         set_error("no kernel for this combination of wheel, threads and search_chunks "
-                  "(wheel 7 supports search_chunks 0, 3, 4)");
+                  "(wheel 7 supports search_chunks 0, 4, 8)");
         return GB_EINVAL;
     }
     CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -571,7 +571,7 @@ using TuneCfg = Ctx::TuneCfg;
 TuneCfg current_cfg()
 {
     return TuneCfg{g.opt.tile_bits, g.opt.threads, g.opt.search_chunks, g.opt.pattern_max,
-                   g.opt.search_pmax};
+                   g.opt.search_pmax, g.opt.tier_b_min};
 }
 
 int apply_cfg(const TuneCfg &c)
@@ -582,6 +582,7 @@ int apply_cfg(const TuneCfg &c)
     g.opt.search_chunks = c.search_chunks;
     g.opt.pattern_max = c.pattern_max;
     g.opt.search_pmax = c.search_pmax;
+    g.opt.tier_b_min = c.tier_b_min;
     g.gkey = GraphKey{};
     return pr ? build_candidates() : GB_OK;
 }
@@ -631,9 +632,9 @@ void load_tune_file()
     FILE *f = fopen(path, "r");
     if (!f) return;
     char key[400];
-    long long a, b, c, d, e;
-    while (fscanf(f, "%399s %lld %lld %lld %lld %lld", key, &a, &b, &c, &d, &e) == 6)
-        g.tuned[key] = TuneCfg{a, b, c, d, e};
+    long long a, b, c, d, e, h;
+    while (fscanf(f, "%399s %lld %lld %lld %lld %lld %lld", key, &a, &b, &c, &d, &e, &h) == 7)
+        g.tuned[key] = TuneCfg{a, b, c, d, e, h};
     fclose(f);
 }
 
@@ -644,9 +645,10 @@ void save_tune_file()
     FILE *f = fopen(path, "w");
     if (!f) return;
     for (const auto &kv : g.tuned)
-        fprintf(f, "%s %lld %lld %lld %lld %lld\n", kv.first.c_str(), (long long)kv.second.tile_bits,
+        fprintf(f, "%s %lld %lld %lld %lld %lld %lld\n", kv.first.c_str(), (long long)kv.second.tile_bits,
                 (long long)kv.second.threads, (long long)kv.second.search_chunks,
-                (long long)kv.second.pattern_max, (long long)kv.second.search_pmax);
+                (long long)kv.second.pattern_max, (long long)kv.second.search_pmax,
+                (long long)kv.second.tier_b_min);
     fclose(f);
 }
 
@@ -668,7 +670,8 @@ int maybe_autotune(CallPlan &cp)
         TuneCfg best = current_cfg();
         float best_ms = time_probe(probe);
         const std::vector<std::pair<int64_t TuneCfg::*, std::vector<int64_t>>> axes = {
-            {&TuneCfg::search_chunks, {2, 3, 4}},
+            {&TuneCfg::search_chunks, {4, 6, 8}},
+            {&TuneCfg::tier_b_min, {4096, 16384, 65536}},
             {&TuneCfg::threads, {512, 1024}},
             {&TuneCfg::tile_bits, {18, 19, 20}},
             {&TuneCfg::pattern_max, {13, 31, 61}},
@@ -987,7 +990,7 @@ const OptDesc kOpts[] = {
     {"bucket_min", &Options::bucket_min, 0, 1 << 22},
     {"bucket_chunk_tiles", &Options::bucket_chunk_tiles, 1, 8192},
     {"search_pmax", &Options::search_pmax, 0, 1 << 20},
-    {"search_chunks", &Options::search_chunks, 0, 4},
+    {"search_chunks", &Options::search_chunks, 0, 8},
     {"autotune", &Options::autotune, 0, 1},
 };
 
@@ -1035,8 +1038,17 @@ struct ServeDev {
     const void *fn = nullptr;
     int nt = 0, grid = 0;
     size_t smem = 0;
+    // bucket pre-pass of served requests: own stream, per-slot arrays from the
+    // stream-ordered pool, released after the request's last batch
+    cudaStream_t pp = nullptr;
+    cudaEvent_t ev_prep = nullptr;
+    unsigned int *d_cnt = nullptr, *d_cur = nullptr;
+    unsigned long long *h_total = nullptr;
+    std::vector<unsigned long long *> bk_off;
+    std::vector<uint32_t *> bk_ent;
 };
 ServeDev sv;
+constexpr uint32_t SERVE_BUCKET_MAX_TILES = 8192;
 }  // namespace
 
 int ctx_serve_begin(int max_slots, int max_items)
@@ -1050,6 +1062,13 @@ int ctx_serve_begin(int max_slots, int max_items)
     CK(cudaEventCreateWithFlags(&sv.ev[0], cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&sv.ev[1], cudaEventDisableTiming));
     if ((rc = dev_alloc(&sv.d_slots, sizeof(SlotDev) * max_slots))) return rc;
+    CK(cudaStreamCreateWithFlags(&sv.pp, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&sv.ev_prep, cudaEventDisableTiming));
+    if ((rc = dev_alloc(&sv.d_cnt, 4ull * (SERVE_BUCKET_MAX_TILES + 1)))) return rc;
+    if ((rc = dev_alloc(&sv.d_cur, 4ull * (SERVE_BUCKET_MAX_TILES + 1)))) return rc;
+    CK(cudaMallocHost((void **)&sv.h_total, 8));
+    sv.bk_off.assign(max_slots, nullptr);
+    sv.bk_ent.assign(max_slots, nullptr);
     if ((rc = dev_alloc(&sv.d_ctrl, sizeof(Ctrl)))) return rc;
     CK(cudaMallocHost((void **)&sv.h_slots, sizeof(SlotDev) * max_slots));
     CK(cudaMallocHost((void **)&sv.h_flags, 4));
@@ -1061,7 +1080,7 @@ int ctx_serve_begin(int max_slots, int max_items)
     sv.nt = (int)g.opt.threads;
     int wheel = (int)g.opt.wheel, bc = (int)g.opt.search_chunks;
     sv.fn = serve_kernel_ptr(wheel, sv.nt, bc);
-    if (!sv.fn) { sv.nt = 512; sv.fn = serve_kernel_ptr(13, 512, 3); }
+    if (!sv.fn) { sv.nt = 1024; sv.fn = serve_kernel_ptr(13, 1024, 8); }
     sv.smem = persistent_smem((uint32_t)g.opt.tile_bits);
     if ((rc = occupancy_grid(sv.fn, sv.nt, sv.smem, &sv.grid))) return rc;
     sv.ready = true;
@@ -1071,8 +1090,19 @@ int ctx_serve_begin(int max_slots, int max_items)
 void ctx_serve_end()
 {
     if (!sv.ready) return;
+    cudaStreamSynchronize(sv.pp);
     cudaStreamSynchronize(sv.st);
     cudaStreamSynchronize(sv.cp);
+    for (size_t i = 0; i < sv.bk_off.size(); i++) {
+        if (sv.bk_off[i]) cudaFreeAsync(sv.bk_off[i], sv.st);
+        if (sv.bk_ent[i]) cudaFreeAsync(sv.bk_ent[i], sv.st);
+    }
+    cudaStreamSynchronize(sv.st);
+    dev_free(&sv.d_cnt, 4ull * (SERVE_BUCKET_MAX_TILES + 1));
+    dev_free(&sv.d_cur, 4ull * (SERVE_BUCKET_MAX_TILES + 1));
+    if (sv.h_total) cudaFreeHost(sv.h_total);
+    if (sv.ev_prep) cudaEventDestroy(sv.ev_prep);
+    if (sv.pp) cudaStreamDestroy(sv.pp);
     dev_free(&sv.d_slots, sizeof(SlotDev) * sv.max_slots);
     dev_free(&sv.d_ctrl, sizeof(Ctrl));
     for (int b = 0; b < 2; b++) {
@@ -1112,8 +1142,27 @@ bool ctx_serve_needs_table(uint64_t lo, uint64_t hi)
     return isqrt_host(cp.n0 + 2 * (cp.n_total - 1)) > g.table_limit;
 }
 
-int ctx_serve_init_slot(int slot, const ServePlan &sp)
+// Upper estimate of the bucket bytes a request needs (admission accounting):
+// hits = n * sum over bucketed primes of 1/p ~ n * ln(ln sqrt(hi) / ln B),
+// 4 bytes each, plus 8 bytes of offsets per tile; 0 when no bucket is used.
+uint64_t ctx_serve_bucket_estimate(uint64_t lo, uint64_t hi)
 {
+    CallPlan cp;
+    if (plan_range(lo, hi, cp) || !cp.n_total) return 0;
+    const uint64_t root = isqrt_host(cp.n0 + 2 * (cp.n_total - 1));
+    const uint64_t B = bucket_bound();
+    if (root < B || cp.ntiles > SERVE_BUCKET_MAX_TILES) return 0;
+    const double w = std::log(std::log((double)root) / std::log((double)B)) + 0.01;
+    return (uint64_t)(4.0 * 1.2 * w * (double)cp.n_total * (1.0 + 32.0 * g.k_words / (1ull << g.opt.tile_bits))) +
+           8ull * (cp.ntiles + 1) + 4096;
+}
+
+// Write the request's params into its slot; when its base primes reach the
+// bucket bound, run the bucket pre-pass for all its tiles on the prep stream
+// (the next batch waits for it).  *bucket_bytes receives what it holds.
+int ctx_serve_init_slot(int slot, const ServePlan &sp, uint64_t *bucket_bytes)
+{
+    *bucket_bytes = 0;
     SlotDev &h = sv.h_slots[slot];
     memset(&h, 0, sizeof h);
     CallPlan cp;
@@ -1123,8 +1172,49 @@ int ctx_serve_init_slot(int slot, const ServePlan &sp)
     cp.nrec = 1;
     fill_params(cp, (uint32_t)g.opt.tile_bits, h.prm);
     h.prm.rec_bits = SERVE_SLOT_SHIFT;
-    CK(cudaMemcpyAsync(&sv.d_slots[slot], &h, sizeof h, cudaMemcpyHostToDevice, sv.st));
+    const uint64_t root = isqrt_host(cp.n0 + 2 * (cp.n_total - 1));
+    const uint64_t B = bucket_bound();
+    if (root < B || cp.ntiles > SERVE_BUCKET_MAX_TILES) {
+        CK(cudaMemcpyAsync(&sv.d_slots[slot], &h, sizeof h, cudaMemcpyHostToDevice, sv.st));
+        return GB_OK;
+    }
+    const uint32_t nt = (uint32_t)cp.ntiles;
+    h.prm.bk_prime0 = count_odd_primes_below(B);
+    Tables t = make_tables();
+    unsigned long long *off = nullptr;
+    uint32_t *ent = nullptr;
+    CK(cudaMemcpyAsync(&sv.d_slots[slot], &h, sizeof h, cudaMemcpyHostToDevice, sv.pp));
+    CK(cudaMallocAsync((void **)&off, 8ull * (nt + 1), sv.pp));
+    CK(cudaMemsetAsync(sv.d_cnt, 0, 4ull * nt, sv.pp));
+    CK(launch_bucket_prepass(sv.pp, 4 * g.sms, &sv.d_slots[slot].prm, t, h.prm.bk_prime0, 0, nt, sv.d_cnt,
+                             off, sv.d_cur, nullptr, 0));
+    CK(cudaMemcpyAsync(sv.h_total, off + nt, 8, cudaMemcpyDeviceToHost, sv.pp));
+    CK(cudaStreamSynchronize(sv.pp));
+    const unsigned long long total = *sv.h_total;
+    CK(cudaMallocAsync((void **)&ent, 4ull * total + 16, sv.pp));
+    CK(launch_bucket_prepass(sv.pp, 4 * g.sms, &sv.d_slots[slot].prm, t, h.prm.bk_prime0, 0, nt, sv.d_cnt,
+                             off, sv.d_cur, ent, 1));
+    h.prm.bk_off = off;
+    h.prm.bk_ent = ent;
+    CK(cudaMemcpyAsync(&sv.d_slots[slot].prm, &h.prm, sizeof h.prm, cudaMemcpyHostToDevice, sv.pp));
+    CK(cudaEventRecord(sv.ev_prep, sv.pp));
+    CK(cudaStreamWaitEvent(sv.st, sv.ev_prep, 0));
+    sv.bk_off[slot] = off;
+    sv.bk_ent[slot] = ent;
+    *bucket_bytes = 8ull * (nt + 1) + 4ull * total + 16;
+    g.stats.kernel_launches += 3;
     return GB_OK;
+}
+
+// Give back a finished request's bucket arrays (stream-ordered after its
+// last batch, which has completed).
+void ctx_serve_release_slot(int slot)
+{
+    if (slot < 0 || slot >= (int)sv.bk_off.size()) return;
+    if (sv.bk_off[slot]) cudaFreeAsync(sv.bk_off[slot], sv.st);
+    if (sv.bk_ent[slot]) cudaFreeAsync(sv.bk_ent[slot], sv.st);
+    sv.bk_off[slot] = nullptr;
+    sv.bk_ent[slot] = nullptr;
 }
 
 unsigned long long *ctx_serve_items(int buf) { return sv.h_items[buf]; }
@@ -1231,8 +1321,8 @@ int gb_set_option(const char *key, int64_t value)
             set_error("bucket_min must be 0 (automatic) or at least 64");
             return GB_EINVAL;
         }
-        if (!strcmp(key, "search_chunks") && value == 1) {
-            set_error("search_chunks must be 0 (per-n search) or 2..4");
+        if (!strcmp(key, "search_chunks") && value != 0 && value != 4 && value != 6 && value != 8) {
+            set_error("search_chunks must be 0 (per-n search), 4, 6 or 8");
             return GB_EINVAL;
         }
         if (!strcmp(key, "wheel") && value != 7 && value != 13) {

@@ -15,6 +15,7 @@ namespace gbk {
 // ---------------------------------------------------------------------------
 
 struct RedScratch {
+    uint32_t tq[32][TQ_CAP];                 // per-warp queues of open n (bit-parallel search)
     unsigned long long arg[32], sum[32], wsum[32], ce[32];
     uint32_t mx[32], slow[32];
     uint32_t hist[HIST_BINS];
@@ -179,6 +180,7 @@ __device__ __forceinline__ void run_tile(const RangeParams &prm, unsigned long l
         } else {
             SubAcc acc;
             acc.reset();
+            TailQueue tq{&s.tq[warp][0], 0u, 0u};
             const uint32_t wbeg = ks >> 5, wend = (ke + 31) >> 5;
             for (uint32_t wb = wbeg + 32u * warp; wb < wend; wb += 32u * NWARP) {
                 const uint32_t w = wb + lane;
@@ -191,8 +193,9 @@ __device__ __forceinline__ void run_tile(const RangeParams &prm, unsigned long l
                 const uint32_t wl = w - wbeg;
                 const uint32_t U = bulk_word<SEARCH_BC>(win, inw ? w : wend - 1u, wl, KW, valid, bb,
                                                         prm.p_max, acc, s.hist);
-                tail_words(win, PR, KW, U, wl, n_lo, ks, i_start, prm, acc, s.hist, ctrl);
+                tail_enqueue(tq, U, wl, win, PR, KW, n_lo, ks, i_start, prm, acc, s.hist, ctrl);
             }
+            tail_flush(tq, win, PR, KW, n_lo, ks, i_start, prm, acc, s.hist, ctrl);
             a.mx = acc.mx;
             a.arg = acc.mx ? kr0 + acc.arg : ~0ull;
             a.sum = acc.sum;

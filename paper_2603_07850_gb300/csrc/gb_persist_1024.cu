@@ -9,15 +9,15 @@ const void *persistent_ptr_1024(int wheel, int bc)
     if (wheel == 13) {
         switch (bc) {
             case 0: return (const void *)persistent_kernel<13, 1024, 0>;
-            case 2: return (const void *)persistent_kernel<13, 1024, 2>;
-            case 3: return (const void *)persistent_kernel<13, 1024, 3>;
             case 4: return (const void *)persistent_kernel<13, 1024, 4>;
+            case 6: return (const void *)persistent_kernel<13, 1024, 6>;
+            case 8: return (const void *)persistent_kernel<13, 1024, 8>;
         }
     } else if (wheel == 7) {
         switch (bc) {
             case 0: return (const void *)persistent_kernel<7, 1024, 0>;
-            case 3: return (const void *)persistent_kernel<7, 1024, 3>;
             case 4: return (const void *)persistent_kernel<7, 1024, 4>;
+            case 8: return (const void *)persistent_kernel<7, 1024, 8>;
         }
     }
     return nullptr;
@@ -25,7 +25,7 @@ const void *persistent_ptr_1024(int wheel, int bc)
 
 const void *serve_ptr_1024(int wheel, int bc)
 {
-    if (wheel == 13 && bc == 3) return (const void *)serve_kernel<13, 1024, 3>;
+    if (wheel == 13 && bc == 8) return (const void *)serve_kernel<13, 1024, 8>;
     if (wheel == 13 && bc == 0) return (const void *)serve_kernel<13, 1024, 0>;
     return nullptr;
 }

@@ -9,15 +9,15 @@ const void *persistent_ptr_256(int wheel, int bc)
     if (wheel == 13) {
         switch (bc) {
             case 0: return (const void *)persistent_kernel<13, 256, 0>;
-            case 2: return (const void *)persistent_kernel<13, 256, 2>;
-            case 3: return (const void *)persistent_kernel<13, 256, 3>;
             case 4: return (const void *)persistent_kernel<13, 256, 4>;
+            case 6: return (const void *)persistent_kernel<13, 256, 6>;
+            case 8: return (const void *)persistent_kernel<13, 256, 8>;
         }
     } else if (wheel == 7) {
         switch (bc) {
             case 0: return (const void *)persistent_kernel<7, 256, 0>;
-            case 3: return (const void *)persistent_kernel<7, 256, 3>;
             case 4: return (const void *)persistent_kernel<7, 256, 4>;
+            case 8: return (const void *)persistent_kernel<7, 256, 8>;
         }
     }
     return nullptr;

@@ -9,15 +9,15 @@ const void *persistent_ptr_512(int wheel, int bc)
     if (wheel == 13) {
         switch (bc) {
             case 0: return (const void *)persistent_kernel<13, 512, 0>;
-            case 2: return (const void *)persistent_kernel<13, 512, 2>;
-            case 3: return (const void *)persistent_kernel<13, 512, 3>;
             case 4: return (const void *)persistent_kernel<13, 512, 4>;
+            case 6: return (const void *)persistent_kernel<13, 512, 6>;
+            case 8: return (const void *)persistent_kernel<13, 512, 8>;
         }
     } else if (wheel == 7) {
         switch (bc) {
             case 0: return (const void *)persistent_kernel<7, 512, 0>;
-            case 3: return (const void *)persistent_kernel<7, 512, 3>;
             case 4: return (const void *)persistent_kernel<7, 512, 4>;
+            case 8: return (const void *)persistent_kernel<7, 512, 8>;
         }
     }
     return nullptr;
@@ -25,7 +25,7 @@ const void *persistent_ptr_512(int wheel, int bc)
 
 const void *serve_ptr_512(int wheel, int bc)
 {
-    if (wheel == 13 && bc == 3) return (const void *)serve_kernel<13, 512, 3>;
+    if (wheel == 13 && bc == 8) return (const void *)serve_kernel<13, 512, 8>;
     if (wheel == 13 && bc == 0) return (const void *)serve_kernel<13, 512, 0>;
     return nullptr;
 }

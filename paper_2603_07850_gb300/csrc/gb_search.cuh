@@ -5,7 +5,8 @@
 // one candidate for the whole word are one funnel shift of two window words
 // by the constant 31 - (i mod 32) (paper Sec. 5.3: bitwise bulk marking,
 // 32 n per instruction).  A lane owns one word and walks the odd primes
-// p < 64 BC in ascending order (compile-time unrolled); each candidate
+// p < 64 BC (BC <= 8, so p < 512) in ascending order (compile-time unrolled);
+// each candidate
 // resolves the bits that are still open:
 //     x  = funnelshift(window words);  nw = x & ~V;  V |= x;
 // and records p in bit-sliced form (plane j gets nw when bit j of p is 1).
@@ -18,7 +19,7 @@
 
 namespace gbk {
 
-constexpr int CAND_COUNT = 53;              // odd primes below 256
+constexpr int CAND_COUNT = 96;             // odd primes below 512
 
 __host__ __device__ constexpr uint32_t cand_prime(int i)
 {
@@ -76,14 +77,57 @@ __host__ __device__ constexpr uint32_t cand_prime(int i)
         case 50: return 239u;
         case 51: return 241u;
         case 52: return 251u;
+        case 53: return 257u;
+        case 54: return 263u;
+        case 55: return 269u;
+        case 56: return 271u;
+        case 57: return 277u;
+        case 58: return 281u;
+        case 59: return 283u;
+        case 60: return 293u;
+        case 61: return 307u;
+        case 62: return 311u;
+        case 63: return 313u;
+        case 64: return 317u;
+        case 65: return 331u;
+        case 66: return 337u;
+        case 67: return 347u;
+        case 68: return 349u;
+        case 69: return 353u;
+        case 70: return 359u;
+        case 71: return 367u;
+        case 72: return 373u;
+        case 73: return 379u;
+        case 74: return 383u;
+        case 75: return 389u;
+        case 76: return 397u;
+        case 77: return 401u;
+        case 78: return 409u;
+        case 79: return 419u;
+        case 80: return 421u;
+        case 81: return 431u;
+        case 82: return 433u;
+        case 83: return 439u;
+        case 84: return 443u;
+        case 85: return 449u;
+        case 86: return 457u;
+        case 87: return 461u;
+        case 88: return 463u;
+        case 89: return 467u;
+        case 90: return 479u;
+        case 91: return 487u;
+        case 92: return 491u;
+        case 93: return 499u;
+        case 94: return 503u;
+        case 95: return 509u;
         default: return 0u;
     }
 }
 
-// Number of candidates below 64 * bc (bc = 1..4): 17, 30, 42, 53.
+// Number of candidates below 64 * bc (bc = 1..8).
 __host__ __device__ constexpr int cand_count(int bc)
 {
-    return bc == 1 ? 17 : bc == 2 ? 30 : bc == 3 ? 42 : 53;
+    return bc == 1 ? 17 : bc == 2 ? 30 : bc == 3 ? 42 : bc == 4 ? 53 : bc == 5 ? 65 : bc == 6 ? 75 : bc == 7 ? 85 : 96;
 }
 
 // sum over the set bits b of x of b
@@ -121,7 +165,7 @@ __device__ __forceinline__ uint32_t bulk_word(const uint32_t *win, uint32_t w, u
 {
     // Every candidate is odd, so plane 0 collects exactly the resolved bits:
     // it doubles as the "already resolved" mask (invalid bits start set).
-    uint32_t B0 = ~valid, B1 = 0, B2 = 0, B3 = 0, B4 = 0, B5 = 0, B6 = 0, B7 = 0;
+    uint32_t B0 = ~valid, B1 = 0, B2 = 0, B3 = 0, B4 = 0, B5 = 0, B6 = 0, B7 = 0, B8 = 0;
 #pragma unroll
     for (int c = 0; c < BC; c++) {
         const uint32_t lo = win[w + KW - 1 - c], hi = win[w + KW - c];
@@ -139,6 +183,7 @@ __device__ __forceinline__ uint32_t bulk_word(const uint32_t *win, uint32_t w, u
                 if (p & 32u) B5 |= x & ~B0;
                 if (p & 64u) B6 |= x & ~B0;
                 if (p & 128u) B7 |= x & ~B0;
+                if (p & 256u) B8 |= x & ~B0;
                 B0 |= x;
             }
         }
@@ -148,10 +193,10 @@ __device__ __forceinline__ uint32_t bulk_word(const uint32_t *win, uint32_t w, u
     const uint32_t R = V & valid;                     // resolved n of this word
     if (R) {
         // sum and sum of b * p over the word, plane by plane
-        const uint32_t Bs[8] = {B0, B1, B2, B3, B4, B5, B6, B7};
+        const uint32_t Bs[9] = {B0, B1, B2, B3, B4, B5, B6, B7, B8};
         uint32_t s = 0, sb = 0;
 #pragma unroll
-        for (int j = 0; j < 8; j++) {
+        for (int j = 0; j < (BC > 4 ? 9 : 8); j++) {
             s += __popc(Bs[j]) << j;
             sb += bitpos_sum(Bs[j]) << j;
         }
@@ -160,14 +205,14 @@ __device__ __forceinline__ uint32_t bulk_word(const uint32_t *win, uint32_t w, u
         // histogram: bin = index of the highest plane that is set
         uint32_t H = 0;
 #pragma unroll
-        for (int j = 7; j >= 1; j--) {
+        for (int j = (BC > 4 ? 8 : 7); j >= 1; j--) {
             acc.h[j] += __popc(Bs[j] & ~H);
             H |= Bs[j];
         }
         // max over the word and its smallest n
         uint32_t cand = R, mx = 0;
 #pragma unroll
-        for (int j = 7; j >= 0; j--) {
+        for (int j = (BC > 4 ? 8 : 7); j >= 0; j--) {
             const uint32_t t = cand & Bs[j];
             if (t) { cand = t; mx |= 1u << j; }
         }
@@ -177,12 +222,95 @@ __device__ __forceinline__ uint32_t bulk_word(const uint32_t *win, uint32_t w, u
     return valid & ~V;
 }
 
-// The open n of a warp's 32 words: compacted 32 at a time across the warp,
-// searched per n from candidate index i_start on, slow path last.
-__device__ __forceinline__ void tail_words(const uint32_t *win, const uint32_t *PR, uint32_t KW,
-                                           uint32_t U, uint32_t wl, unsigned long long n_lo,
-                                           uint32_t ks, uint32_t i_start, const RangeParams &prm,
-                                           SubAcc &acc, uint32_t *s_hist, Ctrl *ctrl)
+// Per-n search of one open n (tile index k) per lane, from candidate index
+// i_start on, then the exact slow path; folds p_min into acc.  Warp-collective
+// (all 32 lanes call it; `act` marks the lanes that hold an n).
+__device__ __forceinline__ void tail_one(const uint32_t *win, const uint32_t *PR, uint32_t KW, uint32_t k,
+                                         bool act, unsigned long long n_lo, uint32_t ks, uint32_t i_start,
+                                         const RangeParams &prm, SubAcc &acc, uint32_t *s_hist, Ctrl *ctrl)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t KB = 32u * KW;
+    const uint32_t t0 = i_start >> 5;
+    const uint32_t mask0 = 0xffffffffu >> (i_start & 31u);
+    const uint32_t kr = k - ks;                           // k relative to the sub-record
+    const unsigned long long n = n_lo + 2ull * k;
+    uint32_t pm = 0;
+    if (act) {
+        if (n == 4ull) {
+            pm = 2u;
+        } else {
+            for (uint32_t t = t0; t < KW; ++t) {
+                const uint32_t s = k + KB - 32u - 32u * t;
+                const uint32_t x = __funnelshift_r(win[s >> 5], win[(s >> 5) + 1], s & 31u);
+                uint32_t m = x & PR[t];
+                if (t == t0) m &= mask0;
+                if (m) { pm = 2u * (32u * t + __clz(m)) + 1u; break; }
+            }
+        }
+    }
+    uint32_t pend = __ballot_sync(GB_FULL_MASK, act && pm == 0u);
+    while (pend) {
+        const int src = __ffs(pend) - 1;
+        pend &= pend - 1;
+        const unsigned long long ns = __shfl_sync(GB_FULL_MASK, n, src);
+        unsigned long long ps = slow_pmin(ns, prm.p_slow_start, prm.slow_cap_log2, ctrl);
+        if (ps >= PMIN_LIMIT) {
+            if (lane == 0) atomicOr(&ctrl->flags, F_OVERFLOW);
+            ps = PMIN_LIMIT - 1;
+        }
+        if ((int)lane == src) {
+            pm = (uint32_t)ps;
+            if (!ps) acc.ce = acc.ce > ~ns ? acc.ce : ~ns;
+        }
+    }
+    if (act && pm) {
+        acc.take_max(pm, kr);
+        acc.sum += pm;
+        acc.wsum += (unsigned long long)pm * (kr + 1ull);
+        acc.slow += pm > prm.p_max ? 1u : 0u;
+        const uint32_t bin = 31u - __clz(pm);
+        if (bin <= 8) {
+#pragma unroll
+            for (uint32_t hb = 1; hb <= 8; hb++) acc.h[hb] += bin == hb ? 1u : 0u;
+        } else {
+            atomicAdd(&s_hist[bin], 1u);
+        }
+    }
+}
+
+// Open n of a warp, queued across its word groups in shared memory so that
+// every per-n round runs 32 full lanes (a group alone holds only ~2-3 % of
+// its 1,024 n).  head/count are warp-uniform.
+constexpr uint32_t TQ_CAP = 96;
+struct TailQueue {
+    uint32_t *q;
+    uint32_t head, count;
+};
+
+__device__ __forceinline__ void tail_round(TailQueue &tq, uint32_t m, const uint32_t *win, const uint32_t *PR,
+                                           uint32_t KW, unsigned long long n_lo, uint32_t ks, uint32_t i_start,
+                                           const RangeParams &prm, SubAcc &acc, uint32_t *s_hist, Ctrl *ctrl)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const bool act = lane < m;
+    uint32_t idx = tq.head + lane;
+    if (idx >= TQ_CAP) idx -= TQ_CAP;
+    const uint32_t k = act ? tq.q[idx] : ks;
+    __syncwarp();
+    tail_one(win, PR, KW, k, act, n_lo, ks, i_start, prm, acc, s_hist, ctrl);
+    tq.head += m;
+    if (tq.head >= TQ_CAP) tq.head -= TQ_CAP;
+    tq.count -= m;
+}
+
+// Append the open bits U of this lane's word (word wl of the sub-record) and
+// run every full round.  A group too large for the queue (only when P_max or
+// the bit-parallel bound is tiny) is run directly in rounds of 32.
+__device__ __forceinline__ void tail_enqueue(TailQueue &tq, uint32_t U, uint32_t wl, const uint32_t *win,
+                                             const uint32_t *PR, uint32_t KW, unsigned long long n_lo,
+                                             uint32_t ks, uint32_t i_start, const RangeParams &prm,
+                                             SubAcc &acc, uint32_t *s_hist, Ctrl *ctrl)
 {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t cnt = __popc(U);
@@ -193,71 +321,48 @@ __device__ __forceinline__ void tail_words(const uint32_t *win, const uint32_t *
         if (lane >= (uint32_t)o) incl += y;
     }
     const uint32_t total = __shfl_sync(GB_FULL_MASK, incl, 31);
-    const uint32_t excl = incl - cnt;
-    const uint32_t KB = 32u * KW;
-    const uint32_t t0 = i_start >> 5;
-    const uint32_t mask0 = 0xffffffffu >> (i_start & 31u);
-    for (uint32_t r = 0; r < total; r += 32) {
-        const uint32_t gi = r + lane;
-        const bool act = gi < total;
-        // owner lane: the number of lanes whose inclusive count is <= gi
-        uint32_t o = 0;
+    if (!total) return;
+    if (tq.count + total > TQ_CAP) {
+        // overflow: redistribute this group directly, 32 open n per round
+        const uint32_t excl = incl - cnt;
+        for (uint32_t r = 0; r < total; r += 32) {
+            const uint32_t gi = r + lane;
+            const bool act = gi < total;
+            uint32_t o = 0;
 #pragma unroll
-        for (uint32_t st = 16; st > 0; st >>= 1) {
-            const uint32_t v = __shfl_sync(GB_FULL_MASK, incl, (o + st - 1) & 31);
-            if (v <= gi) o += st;
-        }
-        o &= 31;
-        const uint32_t Uo = __shfl_sync(GB_FULL_MASK, U, o);
-        const uint32_t eo = __shfl_sync(GB_FULL_MASK, excl, o);
-        const uint32_t wlo = __shfl_sync(GB_FULL_MASK, wl, o);
-        const uint32_t b = act ? __fns(Uo, 0, (int)(gi - eo) + 1) : 0u;
-        const uint32_t kr = 32u * wlo + b;            // k relative to ks
-        const uint32_t k = ks + kr;                   // k within the tile
-        const unsigned long long n = n_lo + 2ull * k;
-        uint32_t pm = 0;
-        if (act) {
-            if (n == 4ull) {
-                pm = 2u;
-            } else {
-                for (uint32_t t = t0; t < KW; ++t) {
-                    const uint32_t s = k + KB - 32u - 32u * t;
-                    const uint32_t x = __funnelshift_r(win[s >> 5], win[(s >> 5) + 1], s & 31u);
-                    uint32_t m = x & PR[t];
-                    if (t == t0) m &= mask0;
-                    if (m) { pm = 2u * (32u * t + __clz(m)) + 1u; break; }
-                }
+            for (uint32_t st = 16; st > 0; st >>= 1) {
+                const uint32_t v = __shfl_sync(GB_FULL_MASK, incl, (o + st - 1) & 31);
+                if (v <= gi) o += st;
             }
+            o &= 31;
+            const uint32_t Uo = __shfl_sync(GB_FULL_MASK, U, o);
+            const uint32_t eo = __shfl_sync(GB_FULL_MASK, excl, o);
+            const uint32_t wlo = __shfl_sync(GB_FULL_MASK, wl, o);
+            const uint32_t b = act ? __fns(Uo, 0, (int)(gi - eo) + 1) : 0u;
+            tail_one(win, PR, KW, ks + 32u * wlo + b, act, n_lo, ks, i_start, prm, acc, s_hist, ctrl);
         }
-        uint32_t pend = __ballot_sync(GB_FULL_MASK, act && pm == 0u);
-        while (pend) {
-            const int src = __ffs(pend) - 1;
-            pend &= pend - 1;
-            const unsigned long long ns = __shfl_sync(GB_FULL_MASK, n, src);
-            unsigned long long ps = slow_pmin(ns, prm.p_slow_start, prm.slow_cap_log2, ctrl);
-            if (ps >= PMIN_LIMIT) {
-                if (lane == 0) atomicOr(&ctrl->flags, F_OVERFLOW);
-                ps = PMIN_LIMIT - 1;
-            }
-            if ((int)lane == src) {
-                pm = (uint32_t)ps;
-                if (!ps) acc.ce = acc.ce > ~ns ? acc.ce : ~ns;
-            }
-        }
-        if (act && pm) {
-            acc.take_max(pm, kr);
-            acc.sum += pm;
-            acc.wsum += (unsigned long long)pm * (kr + 1ull);
-            acc.slow += pm > prm.p_max ? 1u : 0u;
-            const uint32_t bin = 31u - __clz(pm);
-            if (bin <= 8) {
-#pragma unroll
-                for (uint32_t hb = 1; hb <= 8; hb++) acc.h[hb] += bin == hb ? 1u : 0u;
-            } else {
-                atomicAdd(&s_hist[bin], 1u);
-            }
-        }
+        return;
     }
+    uint32_t pos = tq.head + tq.count + incl - cnt;
+    uint32_t u = U;
+    while (u) {
+        const uint32_t b = __ffs(u) - 1;
+        u &= u - 1;
+        uint32_t at = pos++;
+        while (at >= TQ_CAP) at -= TQ_CAP;
+        tq.q[at] = ks + 32u * wl + b;
+    }
+    __syncwarp();
+    tq.count += total;
+    while (tq.count >= 32)
+        tail_round(tq, 32, win, PR, KW, n_lo, ks, i_start, prm, acc, s_hist, ctrl);
+}
+
+__device__ __forceinline__ void tail_flush(TailQueue &tq, const uint32_t *win, const uint32_t *PR, uint32_t KW,
+                                           unsigned long long n_lo, uint32_t ks, uint32_t i_start,
+                                           const RangeParams &prm, SubAcc &acc, uint32_t *s_hist, Ctrl *ctrl)
+{
+    if (tq.count) tail_round(tq, tq.count, win, PR, KW, n_lo, ks, i_start, prm, acc, s_hist, ctrl);
 }
 
 }  // namespace gbk

@@ -46,6 +46,7 @@ struct Req {
     int slot = -1;
     uint64_t next_tile = 0;
     uint64_t table_bytes = 0;
+    uint64_t bucket_est = 0, bucket_bytes = 0;  // bucket pre-pass: estimate, then actual
     bool done = false;
     gb_result res{};
     int status = GB_PENDING;
@@ -69,6 +70,7 @@ struct Serve {
     uint64_t next_id = 1;
     uint64_t submitted = 0, completed = 0, rejected = 0;
     size_t max_items = 0;                      // capacity of each work-list buffer
+    uint64_t live_bucket_bytes = 0;            // bucket arrays of admitted requests
 };
 
 Serve s;
@@ -83,6 +85,20 @@ uint64_t table_bytes_for(uint64_t hi)
     L -= 1.0;
     if (L < 65536.0) return 0;
     return (uint64_t)(12.0 * 1.26 * L / std::log(L));
+}
+
+// Free a request's slot and its bucket arrays (caller holds s.mu).
+void release(Req &r)
+{
+    if (r.slot < 0) return;
+    {
+        std::lock_guard<std::recursive_mutex> ck(ctx_mutex());
+        ctx_serve_release_slot(r.slot);
+    }
+    s.live_bucket_bytes -= std::min(s.live_bucket_bytes, r.bucket_bytes);
+    r.bucket_bytes = 0;
+    s.free_slots.push_back(r.slot);
+    r.slot = -1;
 }
 
 void finish(Req &r, int status, const gb_result *res)
@@ -118,7 +134,8 @@ void worker_loop()
                 uint64_t tb = 0;
                 for (uint64_t id : s.active) tb = std::max(tb, s.reqs.at(id).table_bytes);
                 tb = std::max(tb, r.table_bytes);
-                if (tb + (s.active.size() + 1) * slot_bytes > budget) break;   // wait for room
+                if (tb + (s.active.size() + 1) * slot_bytes + s.live_bucket_bytes + r.bucket_est > budget)
+                    break;                                             // wait for room
                 bool grow;
                 {
                     std::lock_guard<std::recursive_mutex> ck(ctx_mutex());
@@ -131,12 +148,13 @@ void worker_loop()
                     rc = ctx_serve_plan(r.lo, r.hi, &r.sp);
                     if (rc == GB_OK && r.sp.n_total) {
                         r.slot = s.free_slots.back();
-                        rc = ctx_serve_init_slot(r.slot, r.sp);
+                        rc = ctx_serve_init_slot(r.slot, r.sp, &r.bucket_bytes);
+                        if (rc == GB_OK) s.live_bucket_bytes += r.bucket_bytes;
                     }
                 }
                 s.pending.pop_front();
                 if (rc != GB_OK || !r.sp.n_total) {
-                    if (r.slot >= 0) { s.free_slots.push_back(r.slot); r.slot = -1; }
+                    if (r.slot >= 0) release(r);
                     finish(r, rc, nullptr);
                     s.cv_done.notify_all();
                     continue;
@@ -176,7 +194,7 @@ void worker_loop()
                 std::lock_guard<std::mutex> lk(s.mu);
                 for (uint64_t id : s.active) {
                     Req &r = s.reqs.at(id);
-                    s.free_slots.push_back(r.slot);
+                    release(r);
                     finish(r, rc, nullptr);
                 }
                 s.active.clear();
@@ -197,12 +215,12 @@ void worker_loop()
             if (rc == GB_ETIMEOUT) {
                 // report at once: every admitted and every pending request fails.
                 // Their slots are taken now: gb_poll may erase a finished request.
-                std::vector<int> held;
+                std::vector<std::pair<int, uint64_t>> held;
                 {
                     std::lock_guard<std::mutex> lk(s.mu);
                     for (uint64_t id : s.active) {
                         Req &r = s.reqs.at(id);
-                        held.push_back(r.slot);
+                        held.emplace_back(r.slot, r.bucket_bytes);
                         r.slot = -1;
                         finish(r, GB_ETIMEOUT, nullptr);
                     }
@@ -217,7 +235,12 @@ void worker_loop()
                 for (auto &o : inflight) ctx_serve_wait(o.buf, &f, -1);
                 inflight.clear();
                 std::lock_guard<std::mutex> lk(s.mu);
-                for (int sl : held) s.free_slots.push_back(sl);
+                for (auto &h : held) {
+                    Req tmp;
+                    tmp.slot = h.first;
+                    tmp.bucket_bytes = h.second;
+                    release(tmp);
+                }
                 continue;
             }
             std::vector<std::pair<uint64_t, gb_result>> out;
@@ -239,8 +262,7 @@ void worker_loop()
             std::lock_guard<std::mutex> lk(s.mu);
             for (auto &pr : out) {
                 Req &r = s.reqs.at(pr.first);
-                s.free_slots.push_back(r.slot);
-                r.slot = -1;
+                release(r);
                 for (size_t i = 0; i < s.active.size(); i++)
                     if (s.active[i] == r.id) { s.active.erase(s.active.begin() + i); break; }
                 finish(r, pr.second.status, &pr.second);
@@ -321,10 +343,11 @@ int gb_submit(uint64_t lo, uint64_t hi, uint64_t *ticket)
     r.lo = lo;
     r.hi = hi;
     r.table_bytes = table_bytes_for(hi);
+    r.bucket_est = ctx_serve_bucket_estimate(lo, hi);
     r.submit_ns = now_ns();
-    if (r.table_bytes + ctx_serve_slot_bytes() > budget) {
+    if (r.table_bytes + r.bucket_est + ctx_serve_slot_bytes() > budget) {
         s.rejected++;
-        ctx_error("gb_submit: the request's base-prime table exceeds the memory budget");
+        ctx_error("gb_submit: the request's base-prime table and buckets exceed the memory budget");
         return GB_ENOMEM;
     }
     s.reqs[r.id] = r;

@@ -23,7 +23,9 @@ int ctx_serve_begin(int max_slots, int max_items);
 void ctx_serve_end();
 int ctx_serve_plan(uint64_t lo, uint64_t hi, ServePlan *sp);
 bool ctx_serve_needs_table(uint64_t lo, uint64_t hi);
-int ctx_serve_init_slot(int slot, const ServePlan &sp);
+uint64_t ctx_serve_bucket_estimate(uint64_t lo, uint64_t hi);
+int ctx_serve_init_slot(int slot, const ServePlan &sp, uint64_t *bucket_bytes);
+void ctx_serve_release_slot(int slot);
 unsigned long long *ctx_serve_items(int buf);
 int ctx_serve_launch(int buf, size_t n);
 // timeout_ms < 0: wait without bound

@@ -6,6 +6,8 @@ import pytest
 
 pytestmark = pytest.mark.gpu
 
+KEYS = ("tile_bits", "threads", "search_chunks", "pattern_max", "search_pmax", "tier_b_min")
+
 
 def test_autotune_keeps_results_and_caches(tmp_path, monkeypatch):
     from paper_2603_07850_gb300 import binding as gb, build
@@ -19,17 +21,14 @@ def test_autotune_keeps_results_and_caches(tmp_path, monkeypatch):
         ref = gb.gb_verify_range_segments(lo, hi, 4096)
         gb.gb_set_option("autotune", 1)
         got = gb.gb_verify_range_segments(lo, hi, 4096)
-        tuned = {k: gb.gb_get_option(k) for k in ("tile_bits", "threads", "search_chunks",
-                                                  "pattern_max", "search_pmax")}
+        tuned = {k: gb.gb_get_option(k) for k in KEYS}
         again = gb.gb_verify_range_segments(lo, hi, 4096)          # cached choice
     finally:
         gb.gb_shutdown()
     assert (got[0] == ref[0]).all() and (again[0] == ref[0]).all()
     assert got[1] == ref[1] == again[1]
     lines = cache.read_text().split("\n")
-    assert any(l.split()[1:] == [str(tuned[k]) for k in ("tile_bits", "threads", "search_chunks",
-                                                          "pattern_max", "search_pmax")]
-               for l in lines if l)
+    assert any(l.split()[1:] == [str(tuned[k]) for k in KEYS] for l in lines if l)
     # a fresh context reads the saved choice
     gb.gb_init(1 << 16, 20)
     try:

@@ -94,6 +94,10 @@ def test_small_ranges(gb, lo, hi, seg_bits, tile_bits):
     {"threads": 1024, "tier_b_min": 64},
     {"threads": 512, "tier_b_min": 60000, "ctas_per_sm": 1},
     {"use_graph": 0},
+    {"search_chunks": 0},
+    {"search_chunks": 4, "threads": 512},
+    {"search_chunks": 6},
+    {"wheel": 7, "search_chunks": 4},
 ])
 def test_kernel_options_do_not_change_records(gb, opts):
     check_against_oracle(gb, 4, 2_000_001, 1 << 16, 14, tile_bits=17, **opts)
