@@ -266,6 +266,16 @@ int gb_submit(uint64_t lo, uint64_t hi, uint64_t *ticket);
 int gb_poll(uint64_t ticket, gb_result *out, int32_t timeout_ms);
 
 /* ---- introspection --------------------------------------------------------- */
+
+/*
+ * gb_progress -- progress of the gb_verify_range* call that is running (or
+ * finished last): tiles done and tiles in total (segments for the plain
+ * form).  Callable from any thread while the call runs, without waiting for
+ * it: the persistent kernel counts finished tiles into mapped host memory
+ * (paper Sec. 3.2, the progress monitor).  Returns GB_OK or GB_EINVAL.
+ */
+int gb_progress(uint64_t *tiles_done, uint64_t *tiles_total);
+
 int gb_stats(gb_stats_t *out);
 const char *gb_last_error(void);
 

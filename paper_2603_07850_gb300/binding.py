@@ -101,6 +101,7 @@ def load(path: str = LIB_PATH):
         "gb_submit": ([U64, U64, P(U64)], ctypes.c_int),
         "gb_poll": ([U64, P(GbResult), i32], ctypes.c_int),
         "gb_stats": ([P(GbStats)], ctypes.c_int),
+        "gb_progress": ([P(U64), P(U64)], ctypes.c_int),
         "gb_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -196,6 +197,13 @@ def gb_poll(ticket: int, timeout_ms: int = -1):
         return rc, None
     _check("gb_poll", rc, ok=(GB_OK, GB_COUNTEREXAMPLE))
     return rc, r.as_dict()
+
+
+def gb_progress():
+    """(tiles done, tiles total) of the running or last verification call."""
+    d, t = U64(0), U64(0)
+    _check("gb_progress", load().gb_progress(ctypes.byref(d), ctypes.byref(t)))
+    return d.value, t.value
 
 
 def gb_stats() -> dict:

@@ -103,6 +103,7 @@ struct Ctx {
     gb_stats_t stats{};
     size_t device_bytes = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // persistent-kernel timing (time_kernel)
+    unsigned long long *h_progress = nullptr, *d_progress = nullptr;   // mapped tile counter
     // bucket pre-pass buffers
     unsigned int *d_bk_counts = nullptr, *d_bk_cursor = nullptr;
     unsigned long long *d_bk_off = nullptr;
@@ -118,6 +119,8 @@ struct Ctx {
 
 Ctx g;
 std::atomic<bool> g_ready{false};        // gb_init done: readable without the context lock
+std::atomic<unsigned long long> g_progress_total{0};   // tiles of the running call
+std::atomic<unsigned long long *> g_progress_ptr{nullptr};
 uint32_t search_pmax();
 int build_candidates();
 std::recursive_mutex g_mu;
@@ -394,6 +397,7 @@ void fill_params(const CallPlan &cp, uint32_t tile_bits, RangeParams &p)
     p.tile_end = cp.ntiles;
     p.bk_off = nullptr;
     p.bk_ent = nullptr;
+    p.progress = g.d_progress;
 }
 
 void empty_result(gb_result *out)
@@ -401,6 +405,12 @@ void empty_result(gb_result *out)
     if (!out) return;
     memset(out, 0, sizeof *out);
     out->status = GB_OK;
+}
+
+void begin_progress(uint64_t tiles)
+{
+    if (g.h_progress) *(volatile unsigned long long *)g.h_progress = 0;
+    g_progress_total = tiles;
 }
 
 int prepare_common(const CallPlan &cp)
@@ -707,6 +717,7 @@ int run_persistent(uint64_t lo, uint64_t hi, CallPlan &cp)
     if (!cp.n_total) return GB_OK;
     if ((rc = prepare_common(cp))) return rc;
     if ((rc = maybe_autotune(cp))) return rc;
+    begin_progress(cp.ntiles);
     const uint32_t tile_bits = (uint32_t)g.opt.tile_bits;
     const int nt = (int)g.opt.threads;
     const size_t smem = persistent_smem(tile_bits);
@@ -826,6 +837,7 @@ int run_plain(uint64_t lo, uint64_t hi, CallPlan &cp)
     CK(cudaMemcpyAsync(g.d_params, g.h_params, sizeof(RangeParams), cudaMemcpyHostToDevice, g.stream));
     CK(launch_clear(g.stream, g.d_params, g.d_recs, g.d_ctrl, 1, 4 * g.sms));
     const uint64_t nseg = ((cp.n_total - 1) >> sbits) + 1;
+    begin_progress(nseg);
     const uint32_t chunk = (uint32_t)std::min<uint64_t>(1ull << 14, 1ull << g.seg_bits);
     uint64_t launches = 1;
     for (uint64_t s = 0; s < nseg; s++) {
@@ -845,6 +857,7 @@ int run_plain(uint64_t lo, uint64_t hi, CallPlan &cp)
         // the per-segment status round trip of the paper's worker loop
         CK(cudaMemcpyAsync(g.h_flags, &g.d_ctrl->flags, 4, cudaMemcpyDeviceToHost, g.stream));
         CK(cudaStreamSynchronize(g.stream));
+        *(volatile unsigned long long *)g.h_progress += 1;    // one segment done
         launches += 3;
     }
     CK(launch_merge(g.stream, merge_grid_for(cp.nrec), g.d_params, g.d_recs, g.d_ctrl, g.d_parts,
@@ -881,6 +894,8 @@ void release_all()
     if (g.h_params) cudaFreeHost(g.h_params);
     if (g.h_result) cudaFreeHost(g.h_result);
     if (g.h_flags) cudaFreeHost(g.h_flags);
+    g_progress_ptr = nullptr;
+    if (g.h_progress) cudaFreeHost(g.h_progress);
     if (g.stream) cudaStreamDestroy(g.stream);
     if (g.ev0) cudaEventDestroy(g.ev0);
     if (g.ev1) cudaEventDestroy(g.ev1);
@@ -958,6 +973,10 @@ int init_locked(uint32_t p_max, uint32_t seg_bits)
     CK(cudaMallocHost((void **)&g.h_params, sizeof(RangeParams)));
     CK(cudaMallocHost((void **)&g.h_result, sizeof(gb_result)));
     CK(cudaMallocHost((void **)&g.h_flags, 4));
+    CK(cudaHostAlloc((void **)&g.h_progress, 64, cudaHostAllocMapped));
+    CK(cudaHostGetDevicePointer((void **)&g.d_progress, g.h_progress, 0));
+    *g.h_progress = 0;
+    g_progress_ptr = g.h_progress;
     memset(&g.stats, 0, sizeof g.stats);
     g.inited = true;
     g_ready = true;
@@ -1440,6 +1459,7 @@ int gb_verify_range_async(uint64_t lo, uint64_t hi, gb_result *dev_out, void *st
     }
     if ((rc = prepare_common(cp))) return rc;
     if ((rc = maybe_autotune(cp))) return rc;          // synchronises while it tunes
+    begin_progress(cp.ntiles);
     const uint32_t tile_bits = (uint32_t)g.opt.tile_bits;
     const int nt = (int)g.opt.threads;
     const size_t smem = persistent_smem(tile_bits);
@@ -1464,6 +1484,16 @@ int gb_verify_range_async(uint64_t lo, uint64_t hi, gb_result *dev_out, void *st
     g.stats.tiles += cp.ntiles;
     g.stats.calls++;
     g.stats.n_verified += cp.n_total;
+    return GB_OK;
+}
+
+int gb_progress(uint64_t *tiles_done, uint64_t *tiles_total)
+{
+    if (!tiles_done || !tiles_total) return GB_EINVAL;
+    const unsigned long long *p = g_progress_ptr.load();
+    if (!p) { set_error("gb_init has not been called"); return GB_EINVAL; }
+    *tiles_done = *(const volatile unsigned long long *)p;
+    *tiles_total = g_progress_total.load();
     return GB_OK;
 }
 

@@ -342,7 +342,8 @@ __device__ __forceinline__ uint32_t first_bit(const WinGeom &g, uint32_t p, unsi
 
 __device__ __forceinline__ void clear_bit(uint32_t *win, uint32_t j)
 {
-    atomicAnd(&win[j >> 5], ~(1u << (j & 31)));
+    // ~(1 << (j mod 32)) as one rotate: a funnel shift of 0xfffffffe with itself
+    atomicAnd(&win[j >> 5], __funnelshift_l(0xfffffffeu, 0xfffffffeu, j));
 }
 
 // Pass 2: cross off the odd multiples of primes[iA0 .. np) in the window.
@@ -359,8 +360,15 @@ __device__ __forceinline__ void mark_pass(uint32_t *win, const WinGeom &g, const
         uint32_t p = t.primes[i];
         uint32_t j0 = first_bit(g, p, t.recip[i]);
         if (j0 == 0xffffffffu) continue;
-        uint32_t step = 32u * p;
-        for (uint32_t j = j0 + lane * p; j < j_end; j += step) clear_bit(win, j);
+        const uint32_t step = 32u * p;                      // <= 2^21: no wrap below
+        uint32_t j = j0 + lane * p;
+        for (; j + 3u * step < j_end; j += 4u * step) {
+            clear_bit(win, j);
+            clear_bit(win, j + step);
+            clear_bit(win, j + 2u * step);
+            clear_bit(win, j + 3u * step);
+        }
+        for (; j < j_end; j += step) clear_bit(win, j);
     }
     // tier B: one lane per prime
     for (uint32_t i = (t.iB0 > t.iA0 ? t.iB0 : t.iA0) + threadIdx.x; i < np; i += NT) {

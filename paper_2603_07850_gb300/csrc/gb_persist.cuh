@@ -235,6 +235,7 @@ persistent_kernel(const RangeParams *__restrict__ prm_g, Tables t, DevRec *__res
         const unsigned long long tile = s.tile;
         if (tile >= prm.tile_end) break;
         run_tile<WHEEL, NT, SEARCH_BC>(prm, tile, t, wpat, PR, win, s, recs, ctrl);
+        if (threadIdx.x == 0 && prm.progress) atomicAdd_system(prm.progress, 1ull);
     }
 }
 
