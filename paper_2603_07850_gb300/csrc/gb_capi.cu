@@ -63,11 +63,13 @@ struct GraphKey {
     int grid = 0, nt = 0, wheel = 0, merge_grid = 0, clear_records = 0;
     size_t smem = 0;
     const void *recs = nullptr;
+    const void *olist = nullptr;
+    uint32_t olist_wcap = 0, olist_ctas = 0;
     bool operator==(const GraphKey &o) const
     {
         return fn == o.fn && grid == o.grid && nt == o.nt && wheel == o.wheel &&
                merge_grid == o.merge_grid && clear_records == o.clear_records && smem == o.smem &&
-               recs == o.recs;
+               recs == o.recs && olist == o.olist && olist_wcap == o.olist_wcap && olist_ctas == o.olist_ctas;
     }
 };
 
@@ -110,6 +112,10 @@ struct Ctx {
     size_t bk_tiles_cap = 0;
     uint32_t *d_bk_ent = nullptr;
     size_t bk_ent_cap = 0;
+    // open-mask slots of the bit-parallel search (see Tables::olist)
+    uint32_t *d_olist = nullptr;
+    size_t olist_cap = 0;
+    uint32_t olist_wcap = 0, olist_ctas = 0;
     std::map<uint64_t, uint32_t> odd_primes_below;  // cache: bound -> #odd primes below it
     char dev_name[256] = {0};
     struct TuneCfg { int64_t tile_bits, threads, search_chunks, pattern_max, search_pmax, tier_b_min; };
@@ -253,18 +259,26 @@ Tables make_tables()
     t.PR = g.d_PR;
     t.nprimes = (uint32_t)g.nprimes;
     t.k_words = g.k_words;
-    // in-register pattern primes: those above the wheel, up to pattern_max
+    // the fill clears every prime above the wheel up to pattern_max: with
+    // wheel 13 by the group patterns 17*19*23 (from 23 on) and 29*31 (from 31
+    // on), the rest by in-register masks
     static const uint32_t pat[14] = {11, 13, 17, 19, 23, 29, 31, 37, 41, 43, 47, 53, 59, 61};
-    t.pat_lo = g.opt.wheel == 13 ? 2u : 0u;
-    uint32_t hi = t.pat_lo;
+    t.groups = 0;
+    if (g.opt.wheel == 13 && g.opt.pattern_max >= 23) t.groups = 1;
+    if (g.opt.wheel == 13 && g.opt.pattern_max >= 31) t.groups = 2;
+    t.pat_lo = g.opt.wheel == 13 ? 2u + (t.groups >= 1 ? 3u : 0u) + (t.groups >= 2 ? 2u : 0u) : 0u;
+    uint32_t hi = g.opt.wheel == 13 ? 2u : 0u;
     while (hi < 14 && pat[hi] <= (uint32_t)g.opt.pattern_max) hi++;
-    t.pat_hi = hi;
+    t.pat_hi = std::max(hi, t.pat_lo);
     uint32_t lim = (uint32_t)g.opt.wheel;
-    if (hi > t.pat_lo) lim = std::max(lim, pat[hi - 1]);
+    if (hi > (g.opt.wheel == 13 ? 2u : 0u)) lim = std::max(lim, pat[hi - 1]);
     t.iA0 = (uint32_t)(std::upper_bound(g.h_small.begin(), g.h_small.end(), lim) - g.h_small.begin());
     t.iB0 = (uint32_t)(std::lower_bound(g.h_small.begin(), g.h_small.end(),
                                         (uint32_t)g.opt.tier_b_min) - g.h_small.begin());
     if (t.iB0 < t.iA0) t.iB0 = t.iA0;
+    t.olist = g.d_olist;
+    t.olist_wcap = g.olist_wcap;
+    t.olist_ctas = g.olist_ctas;
     return t;
 }
 
@@ -438,6 +452,40 @@ int occupancy_grid(const void *fn, int nt, size_t smem, int *grid)
     if (g.opt.ctas_per_sm > 0) per_sm = std::min<int>(per_sm, (int)g.opt.ctas_per_sm);
     *grid = per_sm * g.sms;
     return GB_OK;
+}
+
+// Open-mask slots per warp for the bit-parallel search: one u32 per word of
+// the warp's share of a tile, i.e. 32 x (its groups of 32 words).
+uint32_t olist_slice(int nt)
+{
+    const uint64_t nwarp = (uint64_t)nt / 32;
+    const uint64_t groups = ((1ull << g.opt.tile_bits) + 1024 * nwarp - 1) / (1024 * nwarp);
+    return (uint32_t)(32 * groups);
+}
+
+// The context's open-mask slots for a persistent launch of `grid` CTAs.
+int ensure_olist(int grid, int nt)
+{
+    if (g.opt.search_chunks == 0) { g.olist_wcap = 0; g.olist_ctas = 0; return GB_OK; }
+    const uint32_t wcap = olist_slice(nt);
+    const size_t need = (size_t)grid * (size_t)(nt / 32) * wcap;
+    if (need > g.olist_cap) {
+        dev_free(&g.d_olist, 4 * g.olist_cap);
+        g.olist_cap = 0;
+        int rc;
+        if ((rc = dev_alloc(&g.d_olist, 4 * need))) return rc;
+        g.olist_cap = need;
+    }
+    g.olist_wcap = wcap;
+    g.olist_ctas = (uint32_t)grid;
+    return GB_OK;
+}
+
+// Grid of a persistent launch on the context's stream, with its list.
+int ctx_grid(const void *fn, int nt, size_t smem, int *grid)
+{
+    int rc = occupancy_grid(fn, nt, smem, grid);
+    return rc ? rc : ensure_olist(*grid, nt);
 }
 
 int merge_grid_for(uint64_t nrec)
@@ -619,7 +667,7 @@ float time_probe(const CallPlan &probe_in)
     const void *fn = persistent_kernel_ptr((int)g.opt.wheel, nt, (int)g.opt.search_chunks);
     if (!fn || smem > g.smem_optin) return -1.f;
     int grid = 0;
-    if (occupancy_grid(fn, nt, smem, &grid)) { cudaGetLastError(); return -1.f; }
+    if (ctx_grid(fn, nt, smem, &grid)) { cudaGetLastError(); return -1.f; }
     RangeParams p;
     fill_params(probe, (uint32_t)g.opt.tile_bits, p);
     float best = -1.f;
@@ -723,7 +771,7 @@ int run_persistent(uint64_t lo, uint64_t hi, CallPlan &cp)
     const size_t smem = persistent_smem(tile_bits);
     const void *fn = persistent_kernel_ptr((int)g.opt.wheel, nt, (int)g.opt.search_chunks);
     int grid = 0;
-    if ((rc = occupancy_grid(fn, nt, smem, &grid))) return rc;
+    if ((rc = ctx_grid(fn, nt, smem, &grid))) return rc;
     const int mg = merge_grid_for(cp.nrec);
     if (needs_buckets(cp)) return run_persistent_buckets(cp, grid, smem, mg, g.d_result, g.stream, true);
     fill_params(cp, tile_bits, *g.h_params);
@@ -732,6 +780,7 @@ int run_persistent(uint64_t lo, uint64_t hi, CallPlan &cp)
         GraphKey key;
         key.fn = fn; key.grid = grid; key.nt = nt; key.wheel = (int)g.opt.wheel; key.merge_grid = mg;
         key.clear_records = clear_records; key.smem = smem; key.recs = g.d_recs;
+        key.olist = g.d_olist; key.olist_wcap = g.olist_wcap; key.olist_ctas = g.olist_ctas;
         if (!(key == g.gkey) || !g.gexec) {
             if (g.gexec) { cudaGraphExecDestroy(g.gexec); g.gexec = nullptr; }
             cudaGraph_t graph = nullptr;
@@ -891,6 +940,7 @@ void release_all()
     dev_free(&g.d_bk_cursor, 4 * g.bk_tiles_cap);
     dev_free(&g.d_bk_off, 8 * g.bk_tiles_cap);
     dev_free(&g.d_bk_ent, 4 * g.bk_ent_cap);
+    dev_free(&g.d_olist, 4 * g.olist_cap);
     if (g.h_params) cudaFreeHost(g.h_params);
     if (g.h_result) cudaFreeHost(g.h_result);
     if (g.h_flags) cudaFreeHost(g.h_flags);
@@ -1065,6 +1115,10 @@ struct ServeDev {
     unsigned long long *h_total = nullptr;
     std::vector<unsigned long long *> bk_off;
     std::vector<uint32_t *> bk_ent;
+    // open-mask slots of the serving kernel (its batches run one after another)
+    uint32_t *d_olist = nullptr;
+    size_t olist_cap = 0;
+    uint32_t olist_wcap = 0;
 };
 ServeDev sv;
 constexpr uint32_t SERVE_BUCKET_MAX_TILES = 8192;
@@ -1099,9 +1153,14 @@ int ctx_serve_begin(int max_slots, int max_items)
     sv.nt = (int)g.opt.threads;
     int wheel = (int)g.opt.wheel, bc = (int)g.opt.search_chunks;
     sv.fn = serve_kernel_ptr(wheel, sv.nt, bc);
-    if (!sv.fn) { sv.nt = 1024; sv.fn = serve_kernel_ptr(13, 1024, 8); }
+    if (!sv.fn) { sv.nt = 1024; bc = 8; sv.fn = serve_kernel_ptr(13, 1024, 8); }
     sv.smem = persistent_smem((uint32_t)g.opt.tile_bits);
     if ((rc = occupancy_grid(sv.fn, sv.nt, sv.smem, &sv.grid))) return rc;
+    if (bc != 0) {                                   // the bit-parallel search needs slots
+        sv.olist_wcap = olist_slice(sv.nt);
+        sv.olist_cap = (size_t)sv.grid * (size_t)(sv.nt / 32) * sv.olist_wcap;
+        if ((rc = dev_alloc(&sv.d_olist, 4 * sv.olist_cap))) return rc;
+    }
     sv.ready = true;
     return GB_OK;
 }
@@ -1124,6 +1183,7 @@ void ctx_serve_end()
     if (sv.pp) cudaStreamDestroy(sv.pp);
     dev_free(&sv.d_slots, sizeof(SlotDev) * sv.max_slots);
     dev_free(&sv.d_ctrl, sizeof(Ctrl));
+    dev_free(&sv.d_olist, 4 * sv.olist_cap);
     for (int b = 0; b < 2; b++) {
         dev_free(&sv.d_items[b], 8ull * sv.max_items);
         if (sv.h_items[b]) cudaFreeHost(sv.h_items[b]);
@@ -1243,6 +1303,9 @@ int ctx_serve_launch(int buf, size_t n)
     CK(cudaMemcpyAsync(sv.d_items[buf], sv.h_items[buf], 8ull * n, cudaMemcpyHostToDevice, sv.st));
     CK(cudaMemsetAsync(sv.d_ctrl, 0, sizeof(Ctrl), sv.st));
     Tables t = make_tables();
+    t.olist = sv.d_olist;
+    t.olist_wcap = sv.olist_wcap;
+    t.olist_ctas = sv.d_olist ? (uint32_t)sv.grid : 0u;
     CK(launch_serve(sv.fn, sv.nt, sv.grid, sv.smem, sv.st, sv.d_items[buf], n, sv.d_slots, t, sv.d_ctrl));
     CK(cudaEventRecord(sv.ev[buf], sv.st));
     g.stats.kernel_launches += 1;
@@ -1464,7 +1527,7 @@ int gb_verify_range_async(uint64_t lo, uint64_t hi, gb_result *dev_out, void *st
     const int nt = (int)g.opt.threads;
     const size_t smem = persistent_smem(tile_bits);
     int grid = 0;
-    if ((rc = occupancy_grid(persistent_kernel_ptr((int)g.opt.wheel, nt, (int)g.opt.search_chunks), nt, smem, &grid))) return rc;
+    if ((rc = ctx_grid(persistent_kernel_ptr((int)g.opt.wheel, nt, (int)g.opt.search_chunks), nt, smem, &grid))) return rc;
     if (needs_buckets(cp)) {
         // the pre-pass sizes its buffers on the host, so this form synchronises
         rc = run_persistent_buckets(cp, grid, smem, merge_grid_for(cp.nrec), dev_out, st, false);

@@ -251,60 +251,97 @@ template <int WHEEL> struct WheelM;
 template <> struct WheelM<13> { static constexpr uint32_t M = 3u * 5u * 7u * 11u * 13u; };
 template <> struct WheelM<7> { static constexpr uint32_t M = 3u * 5u * 7u; };
 
-// Wheel pattern words in shared memory: bit u of the pattern is 1 iff 2u+1 is
-// coprime to M; M + 64 bits so any 32-bit run starting below M can be read
-// with one funnel shift.
-template <int WHEEL, int NT>
-__device__ void build_wheel_pattern(uint32_t *pat)
+// Pre-sieved patterns in shared memory.  Bit u of a pattern of period M is 1
+// iff 2u+1 is coprime to M; M + 64 bits are stored so any 32-bit run starting
+// below M is one funnel shift of two words.  The block holds the wheel
+// (3*5*7*11*13 or 3*5*7) and, with wheel 13, two group patterns that the fill
+// may also apply: 17*19*23 and 29*31.
+constexpr uint32_t G1_M = 17u * 19u * 23u;        // 7,429
+constexpr uint32_t G2_M = 29u * 31u;              // 899
+__host__ __device__ constexpr uint32_t pattern_span(uint32_t M) { return ((M + 64 + 31) / 32 + 3) & ~3u; }
+template <int WHEEL>
+__host__ __device__ constexpr uint32_t pattern_block_words()
 {
-    constexpr uint32_t M = WheelM<WHEEL>::M;
-    constexpr uint32_t NW = (M + 64 + 31) / 32;
-    for (uint32_t w = threadIdx.x; w < NW; w += NT) {
+    return pattern_span(WheelM<WHEEL>::M) + (WHEEL == 13 ? pattern_span(G1_M) + pattern_span(G2_M) : 0u);
+}
+
+template <int NT>
+__device__ void build_pattern(uint32_t *pat, uint32_t M, uint32_t p0, uint32_t p1, uint32_t p2, uint32_t p3,
+                              uint32_t p4)
+{
+    const uint32_t nw = (M + 64 + 31) / 32;
+    for (uint32_t w = threadIdx.x; w < nw; w += NT) {
         uint32_t word = 0;
         for (uint32_t b = 0; b < 32; b++) {
-            uint32_t u = (32 * w + b) % M;
-            uint32_t o = 2 * u + 1;
-            bool cop = (o % 3) && (o % 5) && (o % 7);
-            if (WHEEL == 13) cop = cop && (o % 11) && (o % 13);
+            const uint32_t o = 2u * ((32u * w + b) % M) + 1u;
+            const bool cop = (o % p0) && (o % p1) && (o % p2) && (o % p3) && (o % p4);
             word |= (cop ? 1u : 0u) << b;
         }
         pat[w] = word;
     }
 }
 
-// Pass 1: write every window word from the wheel pattern and the in-register
-// masks of the pattern primes, zeroing bits outside [clear_upto, j_end).
 template <int WHEEL, int NT>
-__device__ __forceinline__ void fill_pass(uint32_t *win, const uint32_t *wpat, const WinGeom &g,
-                                          uint32_t pat_lo, uint32_t pat_hi)
+__device__ void build_wheel_pattern(uint32_t *pat)
+{
+    if (WHEEL == 13) {
+        build_pattern<NT>(pat, WheelM<13>::M, 3, 5, 7, 11, 13);
+        uint32_t *g1 = pat + pattern_span(WheelM<13>::M);
+        build_pattern<NT>(g1, G1_M, 17, 19, 23, 17, 17);
+        build_pattern<NT>(g1 + pattern_span(G1_M), G2_M, 29, 31, 29, 29, 29);
+    } else {
+        build_pattern<NT>(pat, WheelM<7>::M, 3, 5, 7, 3, 3);
+    }
+}
+
+// Phase of window word 0 in a pattern of period M: ((wbase - 1) / 2) mod M,
+// exact for negative values; then this thread's first word.
+__device__ __forceinline__ uint32_t pattern_phase(const WinGeom &g, uint32_t M)
+{
+    uint32_t u0 = (uint32_t)(g.half_abs % M);
+    if (g.neg && u0) u0 = M - u0;
+    return (uint32_t)((u0 + 32ull * threadIdx.x) % M);
+}
+
+// The fill loop; REG = some primes are cleared by in-register masks.
+template <int WHEEL, int NT, bool REG>
+__device__ __forceinline__ void fill_words(uint32_t *win, const uint32_t *wpat, const WinGeom &g,
+                                           uint32_t pat_lo, uint32_t pat_hi, bool use1, bool use2)
 {
     constexpr uint32_t M = WheelM<WHEEL>::M;
     constexpr uint32_t STEP_M = (32u * NT) % M;
-    // phase of word 0: u0 = ((wbase - 1) / 2) mod m, exact for negative values
-    uint32_t u0 = (uint32_t)(g.half_abs % M);
-    if (g.neg && u0) u0 = M - u0;
-    uint32_t u = (uint32_t)((u0 + 32ull * threadIdx.x) % M);
+    constexpr uint32_t STEP_1 = (32u * NT) % G1_M, STEP_2 = (32u * NT) % G2_M;
+    const uint32_t *gp1 = wpat + pattern_span(M);
+    const uint32_t *gp2 = gp1 + pattern_span(G1_M);
+    uint32_t u = pattern_phase(g, M);
+    uint32_t u1 = use1 ? pattern_phase(g, G1_M) : 0u;
+    uint32_t u2 = use2 ? pattern_phase(g, G2_M) : 0u;
     uint32_t r[NPAT];
 #pragma unroll
     for (int i = 0; i < NPAT; i++) {
         const uint32_t p = pat_prime(i);
-        uint32_t v = (uint32_t)(g.half_abs % p);
+        uint32_t v = REG ? (uint32_t)(g.half_abs % p) : 0u;
         if (g.neg && v) v = p - v;
-        r[i] = (v + 32u * threadIdx.x) % p;
+        r[i] = REG ? (v + 32u * threadIdx.x) % p : 0u;
     }
     for (uint32_t w = threadIdx.x; w < g.nfill; w += NT) {
-        uint32_t ui = u >> 5, us = u & 31;
-        uint32_t word = __funnelshift_r(wpat[ui], wpat[ui + 1], us);
+        uint32_t word = __funnelshift_r(wpat[u >> 5], wpat[(u >> 5) + 1], u);
+        if (use1) word &= __funnelshift_r(gp1[u1 >> 5], gp1[(u1 >> 5) + 1], u1);
+        if (use2) word &= __funnelshift_r(gp2[u2 >> 5], gp2[(u2 >> 5) + 1], u2);
+        if (REG) {
 #pragma unroll
-        for (int i = 0; i < NPAT; i++) {
-            if (i >= (int)pat_lo && i < (int)pat_hi) {
-                const uint32_t p = pat_prime(i);
-                const uint32_t h = (p - 1) / 2;      // 2u+1 == 0 mod p  <=>  u == h mod p
-                uint32_t b0 = h >= r[i] ? h - r[i] : h + p - r[i];
-                uint32_t clr = (b0 < 32 ? (1u << b0) : 0u);
-                if (p < 32) clr |= (b0 + p < 32 ? (1u << (b0 + p)) : 0u);
-                if (2 * p < 32) clr |= (b0 + 2 * p < 32 ? (1u << (b0 + 2 * p)) : 0u);
-                word &= ~clr;
+            for (int i = 0; i < NPAT; i++) {
+                if (i >= (int)pat_lo && i < (int)pat_hi) {
+                    const uint32_t p = pat_prime(i);
+                    const uint32_t h = (p - 1) / 2;  // 2u+1 == 0 mod p  <=>  u == h mod p
+                    uint32_t b0 = h >= r[i] ? h - r[i] : h + p - r[i];
+                    uint32_t clr = (b0 < 32 ? (1u << b0) : 0u);
+                    if (p < 32) clr |= (b0 + p < 32 ? (1u << (b0 + p)) : 0u);
+                    if (2 * p < 32) clr |= (b0 + 2 * p < 32 ? (1u << (b0 + 2 * p)) : 0u);
+                    word &= ~clr;
+                    r[i] += (32u * NT) % p;
+                    if (r[i] >= p) r[i] -= p;
+                }
             }
         }
         uint32_t jw = 32u * w;
@@ -313,13 +350,21 @@ __device__ __forceinline__ void fill_pass(uint32_t *win, const uint32_t *wpat, c
         win[w] = word;
         u += STEP_M;
         if (u >= M) u -= M;
-#pragma unroll
-        for (int i = 0; i < NPAT; i++) {
-            const uint32_t p = pat_prime(i);
-            r[i] += (32u * NT) % p;
-            if (r[i] >= p) r[i] -= p;
-        }
+        if (use1) { u1 += STEP_1; if (u1 >= G1_M) u1 -= G1_M; }
+        if (use2) { u2 += STEP_2; if (u2 >= G2_M) u2 -= G2_M; }
     }
+}
+
+// Pass 1: write every window word from the wheel pattern, the group patterns
+// (groups = 0, 1 or 2 of them) and the in-register masks of the pattern
+// primes PAT[pat_lo .. pat_hi), zeroing bits outside [clear_upto, j_end).
+template <int WHEEL, int NT>
+__device__ __forceinline__ void fill_pass(uint32_t *win, const uint32_t *wpat, const WinGeom &g,
+                                          uint32_t pat_lo, uint32_t pat_hi, uint32_t groups)
+{
+    const bool use1 = WHEEL == 13 && groups >= 1, use2 = WHEEL == 13 && groups >= 2;
+    if (pat_lo < pat_hi) fill_words<WHEEL, NT, true>(win, wpat, g, pat_lo, pat_hi, use1, use2);
+    else fill_words<WHEEL, NT, false>(win, wpat, g, pat_lo, pat_hi, use1, use2);
 }
 
 // First window bit of the odd multiples of p that are >= max(p^2, wbase).
@@ -340,6 +385,18 @@ __device__ __forceinline__ uint32_t first_bit(const WinGeom &g, uint32_t p, unsi
     return j < g.j_end ? (uint32_t)j : 0xffffffffu;
 }
 
+// Clear mask m in words w, w + p, ... below w_end (unrolled by four).
+__device__ __forceinline__ void mark_words(uint32_t *win, uint32_t w, uint32_t w_end, uint32_t p, uint32_t m)
+{
+    for (; w + 3u * p < w_end; w += 4u * p) {
+        atomicAnd(&win[w], m);
+        atomicAnd(&win[w + p], m);
+        atomicAnd(&win[w + 2u * p], m);
+        atomicAnd(&win[w + 3u * p], m);
+    }
+    for (; w < w_end; w += p) atomicAnd(&win[w], m);
+}
+
 __device__ __forceinline__ void clear_bit(uint32_t *win, uint32_t j)
 {
     // ~(1 << (j mod 32)) as one rotate: a funnel shift of 0xfffffffe with itself
@@ -354,32 +411,54 @@ __device__ __forceinline__ void mark_pass(uint32_t *win, const WinGeom &g, const
     const int warp = threadIdx.x >> 5;
     constexpr int NWARP = NT / 32;
     const uint32_t j_end = g.j_end;
-    // tier A: one warp per prime, lane l clears multiples l, l+32, ... of it
-    uint32_t a_end = t.iB0 < np ? t.iB0 : np;
-    for (uint32_t i = t.iA0 + warp; i < a_end; i += NWARP) {
-        uint32_t p = t.primes[i];
-        uint32_t j0 = first_bit(g, p, t.recip[i]);
-        if (j0 == 0xffffffffu) continue;
-        const uint32_t step = 32u * p;                      // <= 2^21: no wrap below
-        uint32_t j = j0 + lane * p;
-        for (; j + 3u * step < j_end; j += 4u * step) {
-            clear_bit(win, j);
-            clear_bit(win, j + step);
-            clear_bit(win, j + 2u * step);
-            clear_bit(win, j + 3u * step);
+    // tier A: one warp per prime, lane l clears multiples l, l+32, ... of it.
+    // A lane's step, 32 p bits, is exactly p words, so its bit position and
+    // clear mask stay fixed and each mark is one atomicAnd plus an add.
+    const uint32_t a_end = t.iB0 < np ? t.iB0 : np;
+    const uint32_t iA = t.iA0 + warp;
+    uint32_t pa_nx = iA < a_end ? t.primes[iA] : 0u;
+    unsigned long long ma_nx = iA < a_end ? t.recip[iA] : 0ull;
+    for (uint32_t i = iA; i < a_end; i += NWARP) {
+        const uint32_t p = pa_nx;
+        const unsigned long long ma = ma_nx;
+        if (i + NWARP < a_end) {
+            pa_nx = t.primes[i + NWARP];
+            ma_nx = t.recip[i + NWARP];
         }
-        for (; j < j_end; j += step) clear_bit(win, j);
+        const uint32_t j0 = first_bit(g, p, ma);
+        if (j0 == 0xffffffffu) continue;
+        const uint32_t jl = j0 + lane * p;                  // j0 < 2^21, p < 2^16: no wrap
+        if (jl >= j_end) continue;
+        const uint32_t b = jl & 31u;
+        mark_words(win, jl >> 5, (j_end - b + 31u) >> 5,  // words w with 32 w + b < j_end
+                   p, __funnelshift_l(0xfffffffeu, 0xfffffffeu, b));
     }
-    // tier B: one lane per prime
-    for (uint32_t i = (t.iB0 > t.iA0 ? t.iB0 : t.iA0) + threadIdx.x; i < np; i += NT) {
-        uint32_t p = t.primes[i];
-        uint32_t j0 = first_bit(g, p, t.recip[i]);
-        if (j0 == 0xffffffffu) continue;
-        for (uint32_t j = j0;;) {                           // j + p may exceed 2^32: test first
-            clear_bit(win, j);
-            if (j_end - j <= p) break;
-            j += p;
+    // tier B: one lane per prime; the next prime's table entries are loaded
+    // while the current one is marked
+    const uint32_t iB = (t.iB0 > t.iA0 ? t.iB0 : t.iA0) + threadIdx.x;
+    uint32_t p_nx = iB < np ? t.primes[iB] : 0u;
+    unsigned long long m_nx = iB < np ? t.recip[iB] : 0ull;
+    for (uint32_t i = iB; i < np; i += NT) {
+        const uint32_t p = p_nx;
+        const unsigned long long m = m_nx;
+        if (i + NT < np) {
+            p_nx = t.primes[i + NT];
+            m_nx = t.recip[i + NT];
         }
+        uint32_t j = first_bit(g, p, m);
+        if (j == 0xffffffffu) continue;
+        if (p >= j_end) {                                   // one multiple at most
+            clear_bit(win, j);
+            continue;
+        }
+        // p < j_end < 2^21: no index below wraps
+        for (; j + 3u * p < j_end; j += 4u * p) {
+            clear_bit(win, j);
+            clear_bit(win, j + p);
+            clear_bit(win, j + 2u * p);
+            clear_bit(win, j + 3u * p);
+        }
+        for (; j < j_end; j += p) clear_bit(win, j);
     }
 }
 
@@ -390,15 +469,17 @@ __device__ __forceinline__ void fixup_pass(uint32_t *win, const WinGeom &g, uint
 {
     if (threadIdx.x != 0) return;
     if (!g.neg && g.wbase > 61) return;
-    const uint32_t small[18] = {3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37, 41, 43, 47, 53, 59, 61, 0};
     uint32_t lim = pat_hi ? pat_prime((int)pat_hi - 1) : (uint32_t)WHEEL;
     if (lim < (uint32_t)WHEEL) lim = WHEEL;
-    for (int i = 0; small[i] && small[i] <= lim; i++) {
-        unsigned long long q = small[i];
-        unsigned long long d = q - g.wbase;                   // true distance if q >= wbase
-        bool inside = g.neg ? true : (q >= g.wbase);
+#pragma unroll
+    for (int i = -3; i < NPAT; i++) {                         // 3, 5, 7, then 11 .. 61
+        const uint32_t sp = i == -3 ? 3u : i == -2 ? 5u : i == -1 ? 7u : pat_prime(i);
+        if (sp > lim) continue;
+        const unsigned long long q = sp;
+        const unsigned long long d = q - g.wbase;             // true distance if q >= wbase
+        const bool inside = g.neg ? true : (q >= g.wbase);
         if (!inside || q > g.q_hi) continue;
-        unsigned long long j = d >> 1;
+        const unsigned long long j = d >> 1;
         if (j < g.j_end) atomicOr(&win[j >> 5], 1u << (j & 31));
     }
 }
@@ -426,7 +507,7 @@ __device__ __forceinline__ void build_window(uint32_t *win, const uint32_t *wpat
                                              unsigned long long b0 = 0, unsigned long long b1 = 0,
                                              Ctrl *ctrl = nullptr)
 {
-    fill_pass<WHEEL, NT>(win, wpat, g, t.pat_lo, t.pat_hi);
+    fill_pass<WHEEL, NT>(win, wpat, g, t.pat_lo, t.pat_hi, t.groups);
     __syncthreads();
     uint32_t np = count_le(t.primes, t.nprimes, isqrt_u64(g.q_hi));
     if (np > np_cap) np = np_cap;

@@ -185,7 +185,7 @@ slice_sieve_kernel(unsigned long long half_abs, int neg, uint32_t j_end, uint32_
                    uint32_t *__restrict__ gwin, uint32_t gwords)
 {
     extern __shared__ __align__(16) uint32_t smem[];
-    constexpr uint32_t WP = ((WheelM<WHEEL>::M + 64 + 31) / 32 + 3) & ~3u;
+    constexpr uint32_t WP = pattern_block_words<WHEEL>();
     uint32_t *wpat = smem;
     uint32_t *win = smem + WP;
     build_wheel_pattern<WHEEL, NT>(wpat);
@@ -258,6 +258,7 @@ plain_reduce_kernel(const RangeParams *__restrict__ prm_g, const uint32_t *__res
     LaneAcc a;
     a.reset();
     if (threadIdx.x < HIST_BINS) s.hist[threadIdx.x] = 0u;
+    if (threadIdx.x == 0) { s.xslow = 0u; s.xce = 0ull; }
     __syncthreads();
     for (uint32_t k = ks + threadIdx.x; k < ke; k += NT) {
         const uint32_t p = pm[k];
@@ -544,8 +545,7 @@ const void *slice_kernel_ptr(int wheel, int nt)
 
 uint32_t wheel_pattern_words(int wheel)
 {
-    return wheel == 13 ? (((WheelM<13>::M + 64 + 31) / 32 + 3) & ~3u)
-                       : (((WheelM<7>::M + 64 + 31) / 32 + 3) & ~3u);
+    return wheel == 13 ? pattern_block_words<13>() : pattern_block_words<7>();
 }
 
 cudaError_t launch_persistent(int wheel, int nt, int bc, int grid, size_t smem, cudaStream_t st,

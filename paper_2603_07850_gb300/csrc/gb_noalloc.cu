@@ -41,7 +41,8 @@ constexpr uint32_t NA_MAX_KWORDS = 1024;          // P_max <= 2^16
 constexpr uint32_t NA_MAX_RECORDS = 8192;
 constexpr uint32_t NA_MERGE_GRID = 512;
 constexpr size_t NA_PART_SLOT = 320;              // >= sizeof(MergePart)
-constexpr int NA_TILE_BITS = 20, NA_THREADS = 512, NA_WHEEL = 13, NA_SEARCH_BC = 4;
+// the per-n search: the bit-parallel one needs open-mask slots (128 KB per CTA)
+constexpr int NA_TILE_BITS = 20, NA_THREADS = 512, NA_WHEEL = 13, NA_SEARCH_BC = 0;
 
 constexpr size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr size_t OFF_PRIMES = 0;

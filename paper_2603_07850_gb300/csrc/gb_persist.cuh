@@ -15,11 +15,13 @@ namespace gbk {
 // ---------------------------------------------------------------------------
 
 struct RedScratch {
-    uint32_t tq[32][TQ_CAP];                 // per-warp queues of open n (bit-parallel search)
     unsigned long long arg[32], sum[32], wsum[32], ce[32];
     uint32_t mx[32], slow[32];
     uint32_t hist[HIST_BINS];
+    uint32_t xslow;                          // n_slow and counterexample of the sub-record,
+    unsigned long long xce;                  //   folded by lanes of the bit-parallel search
     unsigned long long tile;
+    RangeParams prm;                         // the current tile's call
 };
 
 // Fold one p_min into a lane's running record state.
@@ -83,8 +85,9 @@ __device__ __forceinline__ void reduce_to_record(LaneAcc &a, RedScratch &s, DevR
         unsigned long long ca = warp_min_u64(m == cm ? ar : ~0ull);
         unsigned long long su = warp_sum_u64(lane < NWARP ? s.sum[lane] : 0ull);
         unsigned long long ws = warp_sum_u64(lane < NWARP ? s.wsum[lane] : 0ull);
-        uint32_t sl = __reduce_add_sync(GB_FULL_MASK, lane < NWARP ? s.slow[lane] : 0u);
+        uint32_t sl = __reduce_add_sync(GB_FULL_MASK, lane < NWARP ? s.slow[lane] : 0u) + s.xslow;
         unsigned long long ce = lane < NWARP ? s.ce[lane] : 0ull;
+        if (lane == 0 && s.xce > ce) ce = s.xce;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             unsigned long long v = __shfl_xor_sync(GB_FULL_MASK, ce, o);
@@ -132,6 +135,7 @@ __device__ __forceinline__ void run_tile(const RangeParams &prm, unsigned long l
     if (bb > ps_odd) bb = ps_odd;
     if (bb > prm.p_max) bb = prm.p_max;
     const uint32_t i_start = (bb + 1u) >> 1;
+    const bool ball = SEARCH_BC && bb >= cand_last(SEARCH_BC ? SEARCH_BC : 1);
     const unsigned long long k0 = tile << prm.tile_bits;
     const unsigned long long left = prm.n_total - k0;
     const uint32_t cnt = left < (1ull << prm.tile_bits) ? (uint32_t)left : (1u << prm.tile_bits);
@@ -152,6 +156,7 @@ __device__ __forceinline__ void run_tile(const RangeParams &prm, unsigned long l
         LaneAcc a;
         a.reset();
         if (threadIdx.x < HIST_BINS) s.hist[threadIdx.x] = 0u;
+        if (threadIdx.x == 0) { s.xslow = 0u; s.xce = 0ull; }
         __syncthreads();
         if (SEARCH_BC == 0) {
             for (uint32_t g32 = (ks >> 5) + warp; (g32 << 5) < ke; g32 += NWARP) {
@@ -180,9 +185,14 @@ __device__ __forceinline__ void run_tile(const RangeParams &prm, unsigned long l
         } else {
             SubAcc acc;
             acc.reset();
-            TailQueue tq{&s.tq[warp][0], 0u, 0u};
+            // this warp's open-mask slots (sized by the host for a whole tile)
+            const bool has_list = t.olist && blockIdx.x < t.olist_ctas;
+            uint32_t *mb = has_list ? t.olist + ((size_t)blockIdx.x * NWARP + warp) * t.olist_wcap : nullptr;
+            const uint32_t gmax = has_list ? t.olist_wcap / 32u : 0u;
+            const SubShared ss{s.hist, &s.xslow, &s.xce};
             const uint32_t wbeg = ks >> 5, wend = (ke + 31) >> 5;
-            for (uint32_t wb = wbeg + 32u * warp; wb < wend; wb += 32u * NWARP) {
+            uint32_t gi = 0;
+            for (uint32_t wb = wbeg + 32u * warp; wb < wend; wb += 32u * NWARP, gi++) {
                 const uint32_t w = wb + lane;
                 const bool inw = w < wend;
                 uint32_t valid = 0u;
@@ -191,21 +201,23 @@ __device__ __forceinline__ void run_tile(const RangeParams &prm, unsigned long l
                     valid = (kw0 + 32u <= ke) ? 0xffffffffu : (0xffffffffu >> (32u - (ke - kw0)));
                 }
                 const uint32_t wl = w - wbeg;
-                const uint32_t U = bulk_word<SEARCH_BC>(win, inw ? w : wend - 1u, wl, KW, valid, bb,
-                                                        prm.p_max, acc, s.hist);
-                tail_enqueue(tq, U, wl, win, PR, KW, n_lo, ks, i_start, prm, acc, s.hist, ctrl);
+                const uint32_t wr = inw ? w : wend - 1u;
+                const uint32_t U = ball ? bulk_word<SEARCH_BC, true>(win, wr, wl, KW, valid, bb, acc)
+                                        : bulk_word<SEARCH_BC, false>(win, wr, wl, KW, valid, bb, acc);
+                if (gi < gmax) mb[32u * gi + lane] = U;
             }
-            tail_flush(tq, win, PR, KW, n_lo, ks, i_start, prm, acc, s.hist, ctrl);
+            if (gi > gmax) {                                 // the host sized the slots too small
+                if (lane == 0) atomicOr(&ctrl->flags, F_INTERNAL);
+                gi = gmax;
+            }
+            __syncwarp();
+            open_search<NWARP>(mb, gi, wbeg + 32u * warp, win, PR, KW, n_lo, ks, i_start, prm, acc, ss, ctrl);
             a.mx = acc.mx;
             a.arg = acc.mx ? kr0 + acc.arg : ~0ull;
             a.sum = acc.sum;
             a.wsum = acc.wsum + kr0 * acc.sum;
-            a.slow = acc.slow;
-            a.ce = acc.ce;
-            a.hA = (unsigned long long)acc.h[1] | ((unsigned long long)acc.h[2] << 16) |
-                   ((unsigned long long)acc.h[3] << 32) | ((unsigned long long)acc.h[4] << 48);
-            a.hB = (unsigned long long)acc.h[5] | ((unsigned long long)acc.h[6] << 16) |
-                   ((unsigned long long)acc.h[7] << 32) | ((unsigned long long)acc.h[8] << 48);
+            a.hA = (unsigned long long)acc.h[0] | ((unsigned long long)acc.h[1] << 32);
+            a.hB = (unsigned long long)acc.h[2] | ((unsigned long long)acc.h[3] << 32);
         }
         reduce_to_record<NT>(a, s, rec, ke - ks, whole, ctrl);
     }
@@ -221,9 +233,11 @@ persistent_kernel(const RangeParams *__restrict__ prm_g, Tables t, DevRec *__res
 {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ RedScratch s;
-    constexpr uint32_t WP = ((WheelM<WHEEL>::M + 64 + 31) / 32 + 3) & ~3u;
-    const RangeParams prm = *prm_g;
-    const uint32_t KW = prm.k_words;
+    constexpr uint32_t WP = pattern_block_words<WHEEL>();
+    // the call's parameters live in shared memory, not in registers
+    if (threadIdx.x == 0) s.prm = *prm_g;
+    const RangeParams &prm = s.prm;
+    const uint32_t KW = prm_g->k_words;
     uint32_t *wpat = smem;
     uint32_t *PR = wpat + WP;
     uint32_t *win = PR + ((KW + 3) & ~3u);
@@ -249,7 +263,7 @@ serve_kernel(const unsigned long long *__restrict__ items, unsigned long long n_
 {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ RedScratch s;
-    constexpr uint32_t WP = ((WheelM<WHEEL>::M + 64 + 31) / 32 + 3) & ~3u;
+    constexpr uint32_t WP = pattern_block_words<WHEEL>();
     const uint32_t KW = t.k_words;
     uint32_t *wpat = smem;
     uint32_t *PR = wpat + WP;
@@ -257,15 +271,19 @@ serve_kernel(const unsigned long long *__restrict__ items, unsigned long long n_
     build_wheel_pattern<WHEEL, NT>(wpat);
     for (uint32_t i = threadIdx.x; i < KW; i += NT) PR[i] = t.PR[i];
     for (;;) {
-        if (threadIdx.x == 0) s.tile = atomicAdd(&ctrl->work_ctr, 1ull);
+        __syncthreads();                         // every thread is done with the last tile's params
+        if (threadIdx.x == 0) {
+            const unsigned long long i = atomicAdd(&ctrl->work_ctr, 1ull);
+            s.tile = i;
+            if (i < n_items) s.prm = slots[items[i] >> SERVE_SLOT_SHIFT].prm;
+        }
         __syncthreads();
         const unsigned long long idx = s.tile;
         if (idx >= n_items) break;
         const unsigned long long item = items[idx];
         const unsigned long long slot = item >> SERVE_SLOT_SHIFT;
         const unsigned long long tile = item & ((1ull << SERVE_SLOT_SHIFT) - 1ull);
-        const RangeParams prm = slots[slot].prm;
-        run_tile<WHEEL, NT, SEARCH_BC>(prm, tile, t, wpat, PR, win, s, &slots[slot].acc, ctrl);
+        run_tile<WHEEL, NT, SEARCH_BC>(s.prm, tile, t, wpat, PR, win, s, &slots[slot].acc, ctrl);
     }
 }
 

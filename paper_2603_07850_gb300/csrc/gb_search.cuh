@@ -130,6 +130,12 @@ __host__ __device__ constexpr int cand_count(int bc)
     return bc == 1 ? 17 : bc == 2 ? 30 : bc == 3 ? 42 : bc == 4 ? 53 : bc == 5 ? 65 : bc == 6 ? 75 : bc == 7 ? 85 : 96;
 }
 
+// Largest candidate below 64 * bc (bc = 1..8).
+__host__ __device__ constexpr uint32_t cand_last(int bc)
+{
+    return cand_prime(cand_count(bc) - 1);
+}
+
 // sum over the set bits b of x of b
 __device__ __forceinline__ uint32_t bitpos_sum(uint32_t x)
 {
@@ -139,29 +145,44 @@ __device__ __forceinline__ uint32_t bitpos_sum(uint32_t x)
 
 // Per-lane running state of one sub-record: sums relative to the sub-record
 // start (k_rel = k - ks), converted to record-relative values at the end.
+// The histogram bins 1..8 are 16-bit counts, two to a word (a lane folds at
+// most 2^20 / 256 n of one sub-record).  The rare n_slow and counterexample
+// updates go to the CTA's shared counters instead of registers.
 struct SubAcc {
-    uint32_t mx, arg, slow;                 // max p_min, its k_rel, #(p_min > P_max)
-    unsigned long long sum, wsum, ce;       // sum p, sum p * (k_rel + 1), ~n of a counterexample
-    uint32_t h[9];                          // counts of bins 1..8 (index 0 unused)
+    uint32_t mx, arg;                       // max p_min, its k_rel
+    unsigned long long sum, wsum;           // sum p, sum p * (k_rel + 1)
+    uint32_t h[4];                          // bin b (1..8) in h[(b-1)/2] bits 16((b-1)%2) ..
     __device__ __forceinline__ void reset()
     {
-        mx = 0; arg = 0xffffffffu; slow = 0; sum = 0; wsum = 0; ce = 0;
+        mx = 0; arg = 0xffffffffu; sum = 0; wsum = 0;
 #pragma unroll
-        for (int b = 0; b < 9; b++) h[b] = 0;
+        for (int b = 0; b < 4; b++) h[b] = 0;
     }
     __device__ __forceinline__ void take_max(uint32_t p, uint32_t k)
     {
         if (p > mx || (p == mx && k < arg)) { mx = p; arg = k; }
     }
+    __device__ __forceinline__ uint32_t bin(int b) const
+    {
+        return (h[(b - 1) >> 1] >> (16 * ((b - 1) & 1))) & 0xffffu;
+    }
+};
+
+// CTA-wide counters of one sub-record that lanes touch only rarely.
+struct SubShared {
+    uint32_t *hist;                         // bins >= 9
+    uint32_t *slow;                         // #(p_min > P_max)
+    unsigned long long *ce;                 // max ~n over counterexamples
 };
 
 // One word of the bulk phase: resolves candidates p < 64 BC with p <= bb,
 // folds the resolved bits into acc and returns the still-open bits.  bb never
-// exceeds P_max, so nothing resolved here counts towards n_slow.
-template <int BC>
+// exceeds P_max, so nothing resolved here counts towards n_slow.  ALL = every
+// candidate below 64 BC is <= bb (the usual case), so no candidate is tested
+// against bb at run time.
+template <int BC, bool ALL>
 __device__ __forceinline__ uint32_t bulk_word(const uint32_t *win, uint32_t w, uint32_t wl, uint32_t KW,
-                                              uint32_t valid, uint32_t bb, uint32_t p_max, SubAcc &acc,
-                                              uint32_t *s_hist)
+                                              uint32_t valid, uint32_t bb, SubAcc &acc)
 {
     // Every candidate is odd, so plane 0 collects exactly the resolved bits:
     // it doubles as the "already resolved" mask (invalid bits start set).
@@ -173,7 +194,7 @@ __device__ __forceinline__ uint32_t bulk_word(const uint32_t *win, uint32_t w, u
         for (int ci = 0; ci < cand_count(BC); ci++) {
             const uint32_t p = cand_prime(ci);
             const uint32_t i = (p - 1) >> 1;
-            if ((int)(i >> 5) == c && p <= bb) {
+            if ((int)(i >> 5) == c && (ALL || p <= bb)) {
                 const uint32_t x = __funnelshift_r(lo, hi, 31u - (i & 31u));
                 // plane j gets the newly resolved bits x & ~B0 (one 3-input op each)
                 if (p & 2u) B1 |= x & ~B0;
@@ -206,7 +227,7 @@ __device__ __forceinline__ uint32_t bulk_word(const uint32_t *win, uint32_t w, u
         uint32_t H = 0;
 #pragma unroll
         for (int j = (BC > 4 ? 8 : 7); j >= 1; j--) {
-            acc.h[j] += __popc(Bs[j] & ~H);
+            acc.h[(j - 1) >> 1] += __popc(Bs[j] & ~H) << (16 * ((j - 1) & 1));
             H |= Bs[j];
         }
         // max over the word and its smallest n
@@ -218,7 +239,6 @@ __device__ __forceinline__ uint32_t bulk_word(const uint32_t *win, uint32_t w, u
         }
         acc.take_max(mx, 32u * wl + (uint32_t)(__ffs(cand) - 1));
     }
-    (void)s_hist;
     return valid & ~V;
 }
 
@@ -227,7 +247,7 @@ __device__ __forceinline__ uint32_t bulk_word(const uint32_t *win, uint32_t w, u
 // (all 32 lanes call it; `act` marks the lanes that hold an n).
 __device__ __forceinline__ void tail_one(const uint32_t *win, const uint32_t *PR, uint32_t KW, uint32_t k,
                                          bool act, unsigned long long n_lo, uint32_t ks, uint32_t i_start,
-                                         const RangeParams &prm, SubAcc &acc, uint32_t *s_hist, Ctrl *ctrl)
+                                         const RangeParams &prm, SubAcc &acc, const SubShared &ss, Ctrl *ctrl)
 {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t KB = 32u * KW;
@@ -261,108 +281,95 @@ __device__ __forceinline__ void tail_one(const uint32_t *win, const uint32_t *PR
         }
         if ((int)lane == src) {
             pm = (uint32_t)ps;
-            if (!ps) acc.ce = acc.ce > ~ns ? acc.ce : ~ns;
+            if (!ps) atomicMax(ss.ce, ~ns);
         }
     }
     if (act && pm) {
         acc.take_max(pm, kr);
         acc.sum += pm;
         acc.wsum += (unsigned long long)pm * (kr + 1ull);
-        acc.slow += pm > prm.p_max ? 1u : 0u;
+        if (pm > prm.p_max) atomicAdd(ss.slow, 1u);
         const uint32_t bin = 31u - __clz(pm);
         if (bin <= 8) {
+            const uint32_t hb = bin - 1u, inc = 1u << (16u * (hb & 1u));
 #pragma unroll
-            for (uint32_t hb = 1; hb <= 8; hb++) acc.h[hb] += bin == hb ? 1u : 0u;
+            for (uint32_t q = 0; q < 4; q++) acc.h[q] += (hb >> 1) == q ? inc : 0u;
         } else {
-            atomicAdd(&s_hist[bin], 1u);
+            atomicAdd(&ss.hist[bin], 1u);
         }
     }
 }
 
-// Open n of a warp, queued across its word groups in shared memory so that
-// every per-n round runs 32 full lanes (a group alone holds only ~2-3 % of
-// its 1,024 n).  head/count are warp-uniform.
-constexpr uint32_t TQ_CAP = 96;
-struct TailQueue {
-    uint32_t *q;
-    uint32_t head, count;
-};
-
-__device__ __forceinline__ void tail_round(TailQueue &tq, uint32_t m, const uint32_t *win, const uint32_t *PR,
-                                           uint32_t KW, unsigned long long n_lo, uint32_t ks, uint32_t i_start,
-                                           const RangeParams &prm, SubAcc &acc, uint32_t *s_hist, Ctrl *ctrl)
+// Position of the r-th (0-based) set bit of x; x has more than r set bits.
+__device__ __forceinline__ uint32_t select_bit(uint32_t x, uint32_t r)
 {
-    const uint32_t lane = threadIdx.x & 31;
-    const bool act = lane < m;
-    uint32_t idx = tq.head + lane;
-    if (idx >= TQ_CAP) idx -= TQ_CAP;
-    const uint32_t k = act ? tq.q[idx] : ks;
-    __syncwarp();
-    tail_one(win, PR, KW, k, act, n_lo, ks, i_start, prm, acc, s_hist, ctrl);
-    tq.head += m;
-    if (tq.head >= TQ_CAP) tq.head -= TQ_CAP;
-    tq.count -= m;
+    uint32_t pos = 0;
+#pragma unroll
+    for (uint32_t w = 16; w > 0; w >>= 1) {
+        const uint32_t c = __popc((x >> pos) & ((1u << w) - 1u));
+        if (r >= c) { r -= c; pos += w; }
+    }
+    return pos;
 }
 
-// Append the open bits U of this lane's word (word wl of the sub-record) and
-// run every full round.  A group too large for the queue (only when P_max or
-// the bit-parallel bound is tiny) is run directly in rounds of 32.
-__device__ __forceinline__ void tail_enqueue(TailQueue &tq, uint32_t U, uint32_t wl, const uint32_t *win,
-                                             const uint32_t *PR, uint32_t KW, unsigned long long n_lo,
-                                             uint32_t ks, uint32_t i_start, const RangeParams &prm,
-                                             SubAcc &acc, uint32_t *s_hist, Ctrl *ctrl)
+// The per-n phase of one sub-record for one warp.  During the bulk phase the
+// warp stored the open mask of each of its words (lane l of group gi at
+// mb[32 gi + l], word wg0 + 32 NWARP gi + l); here the open n are gathered
+// group by group -- lane g takes the g-th open bit of the group (a prefix
+// scan of the lanes' counts, a binary search over it, the rank-th set bit of
+// that word) -- into a 32-entry queue held one entry per lane, and every full
+// queue is searched by tail_one.  No loop here diverges with the data except
+// tail_one's own candidate walk.
+template <int NWARP>
+__device__ __forceinline__ void open_search(const uint32_t *mb, uint32_t ngroups, uint32_t wg0,
+                                            const uint32_t *win, const uint32_t *PR, uint32_t KW,
+                                            unsigned long long n_lo, uint32_t ks, uint32_t i_start,
+                                            const RangeParams &prm, SubAcc &acc, const SubShared &ss, Ctrl *ctrl)
 {
     const uint32_t lane = threadIdx.x & 31;
-    const uint32_t cnt = __popc(U);
-    uint32_t incl = cnt;
+    uint32_t kq = ks, c = 0;                           // lanes < c hold a queued n (warp-uniform c)
+    uint32_t U_nx = ngroups ? mb[lane] : 0u;           // the next group's masks load ahead
+    for (uint32_t gi = 0; gi < ngroups; gi++) {
+        const uint32_t U = U_nx;
+        if (gi + 1 < ngroups) U_nx = mb[32u * (gi + 1) + lane];
+        const uint32_t cnt = __popc(U);
+        uint32_t incl = cnt;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(GB_FULL_MASK, incl, o);
-        if (lane >= (uint32_t)o) incl += y;
-    }
-    const uint32_t total = __shfl_sync(GB_FULL_MASK, incl, 31);
-    if (!total) return;
-    if (tq.count + total > TQ_CAP) {
-        // overflow: redistribute this group directly, 32 open n per round
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(GB_FULL_MASK, incl, o);
+            if (lane >= (uint32_t)o) incl += y;
+        }
+        const uint32_t total = __shfl_sync(GB_FULL_MASK, incl, 31);
         const uint32_t excl = incl - cnt;
+        const uint32_t wg = wg0 + 32u * NWARP * gi;
         for (uint32_t r = 0; r < total; r += 32) {
-            const uint32_t gi = r + lane;
-            const bool act = gi < total;
-            uint32_t o = 0;
+            const uint32_t m = total - r < 32u ? total - r : 32u;
+            const uint32_t g = r + lane;
+            uint32_t o = 0;                            // first lane whose inclusive count exceeds g
 #pragma unroll
             for (uint32_t st = 16; st > 0; st >>= 1) {
                 const uint32_t v = __shfl_sync(GB_FULL_MASK, incl, (o + st - 1) & 31);
-                if (v <= gi) o += st;
+                if (v <= g) o += st;
             }
             o &= 31;
             const uint32_t Uo = __shfl_sync(GB_FULL_MASK, U, o);
             const uint32_t eo = __shfl_sync(GB_FULL_MASK, excl, o);
-            const uint32_t wlo = __shfl_sync(GB_FULL_MASK, wl, o);
-            const uint32_t b = act ? __fns(Uo, 0, (int)(gi - eo) + 1) : 0u;
-            tail_one(win, PR, KW, ks + 32u * wlo + b, act, n_lo, ks, i_start, prm, acc, s_hist, ctrl);
+            const uint32_t kn = 32u * (wg + o) + (lane < m ? select_bit(Uo, g - eo) : 0u);
+            // append entries 0..m-1 of kn at queue positions c..c+m-1
+            const uint32_t k_lo = __shfl_sync(GB_FULL_MASK, kn, (lane - c) & 31);
+            const uint32_t k_hi = __shfl_sync(GB_FULL_MASK, kn, (lane + 32u - c) & 31);
+            if (lane >= c && lane - c < m) kq = k_lo;
+            if (c + m >= 32u) {
+                tail_one(win, PR, KW, kq, true, n_lo, ks, i_start, prm, acc, ss, ctrl);
+                const uint32_t left = c + m - 32u;
+                if (lane < left) kq = k_hi;
+                c = left;
+            } else {
+                c += m;
+            }
         }
-        return;
     }
-    uint32_t pos = tq.head + tq.count + incl - cnt;
-    uint32_t u = U;
-    while (u) {
-        const uint32_t b = __ffs(u) - 1;
-        u &= u - 1;
-        uint32_t at = pos++;
-        while (at >= TQ_CAP) at -= TQ_CAP;
-        tq.q[at] = ks + 32u * wl + b;
-    }
-    __syncwarp();
-    tq.count += total;
-    while (tq.count >= 32)
-        tail_round(tq, 32, win, PR, KW, n_lo, ks, i_start, prm, acc, s_hist, ctrl);
-}
-
-__device__ __forceinline__ void tail_flush(TailQueue &tq, const uint32_t *win, const uint32_t *PR, uint32_t KW,
-                                           unsigned long long n_lo, uint32_t ks, uint32_t i_start,
-                                           const RangeParams &prm, SubAcc &acc, uint32_t *s_hist, Ctrl *ctrl)
-{
-    if (tq.count) tail_round(tq, tq.count, win, PR, KW, n_lo, ks, i_start, prm, acc, s_hist, ctrl);
+    if (c) tail_one(win, PR, KW, kq, lane < c, n_lo, ks, i_start, prm, acc, ss, ctrl);
 }
 
 }  // namespace gbk

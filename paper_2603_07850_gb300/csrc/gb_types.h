@@ -75,7 +75,14 @@ struct Tables {
     uint32_t iA0;                      // first prime index that is marked (above the patterns)
     uint32_t iB0;                      // first prime index marked lane-per-prime
     uint32_t pat_lo, pat_hi;           // in-register pattern primes PAT[pat_lo .. pat_hi)
+    uint32_t groups;                   // group patterns in the fill: 1 = 17*19*23, 2 = also 29*31
     uint32_t k_words;
+    // scratch of the bit-parallel search: warp w of CTA c stores the open
+    // mask of each of its words in olist[(c * warps_per_cta + w) * olist_wcap
+    // ..], olist_wcap >= its words per tile; a launch of the bit-parallel
+    // kernels must provide it for CTAs c < olist_ctas = the grid
+    uint32_t *olist;
+    uint32_t olist_wcap, olist_ctas;
 };
 
 }  // namespace gbk
