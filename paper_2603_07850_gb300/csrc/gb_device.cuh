@@ -172,7 +172,9 @@ static __device__ bool is_prime_u64(unsigned long long x)
 // call with the same n).  Returns p_min, or 0 with a flag set: F_COUNTEREX if
 // no p <= n/2 works (the counterexample is recorded), F_SLOWCAP if the
 // candidate cap ran out first.
-static __device__ unsigned long long slow_pmin(unsigned long long n, unsigned long long p_start,
+// Kept out of line: it runs for a tiny share of n, and inlined its 64-bit
+// Montgomery state would weigh on the register allocation of the hot loops.
+static __device__ __noinline__ unsigned long long slow_pmin(unsigned long long n, unsigned long long p_start,
                                         uint32_t cap_log2, Ctrl *ctrl)
 {
     const int lane = threadIdx.x & 31;
@@ -413,25 +415,26 @@ __device__ __forceinline__ void mark_pass(uint32_t *win, const WinGeom &g, const
     const uint32_t j_end = g.j_end;
     // tier A: one warp per prime, lane l clears multiples l, l+32, ... of it.
     // A lane's step, 32 p bits, is exactly p words, so its bit position and
-    // clear mask stay fixed and each mark is one atomicAnd plus an add.
+    // clear mask stay fixed and each mark is one atomicAnd plus an add.  Warp
+    // w takes the primes w, w + NWARP, w + 2 NWARP, ... (the dense small ones
+    // spread over all warps), 32 at a time: lane q finds the first multiple
+    // of the q-th, then the warp marks the 32 primes in turn.
     const uint32_t a_end = t.iB0 < np ? t.iB0 : np;
-    const uint32_t iA = t.iA0 + warp;
-    uint32_t pa_nx = iA < a_end ? t.primes[iA] : 0u;
-    unsigned long long ma_nx = iA < a_end ? t.recip[iA] : 0ull;
-    for (uint32_t i = iA; i < a_end; i += NWARP) {
-        const uint32_t p = pa_nx;
-        const unsigned long long ma = ma_nx;
-        if (i + NWARP < a_end) {
-            pa_nx = t.primes[i + NWARP];
-            ma_nx = t.recip[i + NWARP];
+    for (uint32_t i0 = t.iA0 + warp; i0 < a_end; i0 += 32u * NWARP) {
+        const uint32_t iq = i0 + lane * NWARP;
+        const uint32_t pq = iq < a_end ? t.primes[iq] : 0u;
+        const uint32_t jq = iq < a_end ? first_bit(g, pq, t.recip[iq]) : 0xffffffffu;
+        const uint32_t nq = (a_end - i0 + NWARP - 1) / NWARP;   // primes of this batch
+        for (uint32_t q = 0; q < nq && q < 32u; q++) {
+            const uint32_t j0 = __shfl_sync(GB_FULL_MASK, jq, q);
+            if (j0 == 0xffffffffu) continue;
+            const uint32_t p = __shfl_sync(GB_FULL_MASK, pq, q);
+            const uint32_t jl = j0 + lane * p;              // j0 < 2^21, p < 2^16: no wrap
+            if (jl >= j_end) continue;
+            const uint32_t b = jl & 31u;
+            mark_words(win, jl >> 5, (j_end - b + 31u) >> 5,  // words w with 32 w + b < j_end
+                       p, __funnelshift_l(0xfffffffeu, 0xfffffffeu, b));
         }
-        const uint32_t j0 = first_bit(g, p, ma);
-        if (j0 == 0xffffffffu) continue;
-        const uint32_t jl = j0 + lane * p;                  // j0 < 2^21, p < 2^16: no wrap
-        if (jl >= j_end) continue;
-        const uint32_t b = jl & 31u;
-        mark_words(win, jl >> 5, (j_end - b + 31u) >> 5,  // words w with 32 w + b < j_end
-                   p, __funnelshift_l(0xfffffffeu, 0xfffffffeu, b));
     }
     // tier B: one lane per prime; the next prime's table entries are loaded
     // while the current one is marked

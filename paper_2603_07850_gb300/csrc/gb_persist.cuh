@@ -15,6 +15,7 @@ namespace gbk {
 // ---------------------------------------------------------------------------
 
 struct RedScratch {
+    uint32_t ring[32][64];                   // per-warp rings of open n (bit-parallel search)
     unsigned long long arg[32], sum[32], wsum[32], ce[32];
     uint32_t mx[32], slow[32];
     uint32_t hist[HIST_BINS];
@@ -22,6 +23,7 @@ struct RedScratch {
     unsigned long long xce;                  //   folded by lanes of the bit-parallel search
     unsigned long long tile;
     RangeParams prm;                         // the current tile's call
+    uint32_t one;                            // holds 1 (multiplier of the plane updates)
 };
 
 // Fold one p_min into a lane's running record state.
@@ -190,6 +192,7 @@ __device__ __forceinline__ void run_tile(const RangeParams &prm, unsigned long l
             uint32_t *mb = has_list ? t.olist + ((size_t)blockIdx.x * NWARP + warp) * t.olist_wcap : nullptr;
             const uint32_t gmax = has_list ? t.olist_wcap / 32u : 0u;
             const SubShared ss{s.hist, &s.xslow, &s.xce};
+            const uint32_t one = s.one;                       // 1, a value the compiler cannot see
             const uint32_t wbeg = ks >> 5, wend = (ke + 31) >> 5;
             uint32_t gi = 0;
             for (uint32_t wb = wbeg + 32u * warp; wb < wend; wb += 32u * NWARP, gi++) {
@@ -202,8 +205,8 @@ __device__ __forceinline__ void run_tile(const RangeParams &prm, unsigned long l
                 }
                 const uint32_t wl = w - wbeg;
                 const uint32_t wr = inw ? w : wend - 1u;
-                const uint32_t U = ball ? bulk_word<SEARCH_BC, true>(win, wr, wl, KW, valid, bb, acc)
-                                        : bulk_word<SEARCH_BC, false>(win, wr, wl, KW, valid, bb, acc);
+                const uint32_t U = ball ? bulk_word<SEARCH_BC, true>(win, wr, wl, KW, valid, bb, one, acc)
+                                        : bulk_word<SEARCH_BC, false>(win, wr, wl, KW, valid, bb, one, acc);
                 if (gi < gmax) mb[32u * gi + lane] = U;
             }
             if (gi > gmax) {                                 // the host sized the slots too small
@@ -211,7 +214,8 @@ __device__ __forceinline__ void run_tile(const RangeParams &prm, unsigned long l
                 gi = gmax;
             }
             __syncwarp();
-            open_search<NWARP>(mb, gi, wbeg + 32u * warp, win, PR, KW, n_lo, ks, i_start, prm, acc, ss, ctrl);
+            open_search_ring<NWARP>(mb, gi, wbeg + 32u * warp, &s.ring[warp][0], win, PR, KW, n_lo, ks, i_start,
+                                    prm, acc, ss, ctrl);
             a.mx = acc.mx;
             a.arg = acc.mx ? kr0 + acc.arg : ~0ull;
             a.sum = acc.sum;
@@ -226,8 +230,12 @@ __device__ __forceinline__ void run_tile(const RangeParams &prm, unsigned long l
 // SEARCH_BC = 0: per-n search (one lane per n, 32 candidates per step).
 // SEARCH_BC = 2..4: bit-parallel search of the candidates p < 64 SEARCH_BC
 // (one lane per 32 n), the rest per n after warp compaction.
+// 512-thread CTAs are built for two per SM (64 registers a thread), so that with
+// tiles of at most 2^19 n one CTA can build its window while the other searches.
+template <int NT> constexpr int min_ctas() { return NT == 512 ? 2 : 1; }
+
 template <int WHEEL, int NT, int SEARCH_BC>
-__global__ void __launch_bounds__(NT, 1)
+__global__ void __launch_bounds__(NT, min_ctas<NT>())
 persistent_kernel(const RangeParams *__restrict__ prm_g, Tables t, DevRec *__restrict__ recs,
                   Ctrl *ctrl)
 {
@@ -235,7 +243,7 @@ persistent_kernel(const RangeParams *__restrict__ prm_g, Tables t, DevRec *__res
     __shared__ RedScratch s;
     constexpr uint32_t WP = pattern_block_words<WHEEL>();
     // the call's parameters live in shared memory, not in registers
-    if (threadIdx.x == 0) s.prm = *prm_g;
+    if (threadIdx.x == 0) { s.prm = *prm_g; s.one = 1u; }
     const RangeParams &prm = s.prm;
     const uint32_t KW = prm_g->k_words;
     uint32_t *wpat = smem;
@@ -257,7 +265,7 @@ persistent_kernel(const RangeParams *__restrict__ prm_g, Tables t, DevRec *__res
 // device counter, so the tiles of many requests share one persistent launch;
 // each tile folds into its request's record with atomics.
 template <int WHEEL, int NT, int SEARCH_BC>
-__global__ void __launch_bounds__(NT, 1)
+__global__ void __launch_bounds__(NT, min_ctas<NT>())
 serve_kernel(const unsigned long long *__restrict__ items, unsigned long long n_items, SlotDev *slots,
              Tables t, Ctrl *ctrl)
 {
@@ -270,6 +278,7 @@ serve_kernel(const unsigned long long *__restrict__ items, unsigned long long n_
     uint32_t *win = PR + ((KW + 3) & ~3u);
     build_wheel_pattern<WHEEL, NT>(wpat);
     for (uint32_t i = threadIdx.x; i < KW; i += NT) PR[i] = t.PR[i];
+    if (threadIdx.x == 0) s.one = 1u;
     for (;;) {
         __syncthreads();                         // every thread is done with the last tile's params
         if (threadIdx.x == 0) {

@@ -180,9 +180,13 @@ struct SubShared {
 // exceeds P_max, so nothing resolved here counts towards n_slow.  ALL = every
 // candidate below 64 BC is <= bb (the usual case), so no candidate is tested
 // against bb at run time.
+// `one` is 1, passed at run time: a plane update B += nw * one is then an
+// integer multiply-add, issued on the FMA pipe beside the ALU pipe that runs
+// the funnel shifts and logic ops (the newly resolved bits nw are disjoint
+// from every plane, so the add is an OR).
 template <int BC, bool ALL>
 __device__ __forceinline__ uint32_t bulk_word(const uint32_t *win, uint32_t w, uint32_t wl, uint32_t KW,
-                                              uint32_t valid, uint32_t bb, SubAcc &acc)
+                                              uint32_t valid, uint32_t bb, uint32_t one, SubAcc &acc)
 {
     // Every candidate is odd, so plane 0 collects exactly the resolved bits:
     // it doubles as the "already resolved" mask (invalid bits start set).
@@ -196,15 +200,15 @@ __device__ __forceinline__ uint32_t bulk_word(const uint32_t *win, uint32_t w, u
             const uint32_t i = (p - 1) >> 1;
             if ((int)(i >> 5) == c && (ALL || p <= bb)) {
                 const uint32_t x = __funnelshift_r(lo, hi, 31u - (i & 31u));
-                // plane j gets the newly resolved bits x & ~B0 (one 3-input op each)
-                if (p & 2u) B1 |= x & ~B0;
-                if (p & 4u) B2 |= x & ~B0;
-                if (p & 8u) B3 |= x & ~B0;
-                if (p & 16u) B4 |= x & ~B0;
-                if (p & 32u) B5 |= x & ~B0;
-                if (p & 64u) B6 |= x & ~B0;
-                if (p & 128u) B7 |= x & ~B0;
-                if (p & 256u) B8 |= x & ~B0;
+                const uint32_t nw = x & ~B0;            // newly resolved: plane j gets them
+                if (p & 2u) B1 = nw * one + B1;
+                if (p & 4u) B2 = nw * one + B2;
+                if (p & 8u) B3 = nw * one + B3;
+                if (p & 16u) B4 = nw * one + B4;
+                if (p & 32u) B5 = nw * one + B5;
+                if (p & 64u) B6 = nw * one + B6;
+                if (p & 128u) B7 = nw * one + B7;
+                if (p & 256u) B8 = nw * one + B8;
                 B0 |= x;
             }
         }
@@ -259,14 +263,22 @@ __device__ __forceinline__ void tail_one(const uint32_t *win, const uint32_t *PR
     if (act) {
         if (n == 4ull) {
             pm = 2u;
-        } else {
-            for (uint32_t t = t0; t < KW; ++t) {
-                const uint32_t s = k + KB - 32u - 32u * t;
-                const uint32_t x = __funnelshift_r(win[s >> 5], win[(s >> 5) + 1], s & 31u);
-                uint32_t m = x & PR[t];
-                if (t == t0) m &= mask0;
-                if (m) { pm = 2u * (32u * t + __clz(m)) + 1u; break; }
+        } else if (t0 < KW) {
+            // chunk t covers the 32 window bits from s_t = k + K - 32 - 32 t:
+            // the shift is the same for every t and chunk t+1's high word is
+            // chunk t's low word, so each step loads one window word
+            const uint32_t s0 = k + KB - 32u - 32u * t0;
+            const uint32_t sh = s0 & 31u;
+            uint32_t w = s0 >> 5, hi = win[w + 1];
+            uint32_t lo = win[w];
+            uint32_t m = __funnelshift_r(lo, hi, sh) & PR[t0] & mask0;
+            uint32_t t = t0;
+            while (!m && ++t < KW) {
+                hi = lo;
+                lo = win[--w];
+                m = __funnelshift_r(lo, hi, sh) & PR[t];
             }
+            if (m) pm = 2u * (32u * t + __clz(m)) + 1u;
         }
     }
     uint32_t pend = __ballot_sync(GB_FULL_MASK, act && pm == 0u);
@@ -370,6 +382,48 @@ __device__ __forceinline__ void open_search(const uint32_t *mb, uint32_t ngroups
         }
     }
     if (c) tail_one(win, PR, KW, kq, lane < c, n_lo, ks, i_start, prm, acc, ss, ctrl);
+}
+
+// The same per-n phase with a lower-latency compaction: each step every lane
+// hands over the lowest open bit of its word, its slot in the warp's 64-entry
+// shared ring given by a ballot and a popcount (about three steps per group at
+// 10^12), and a full round of 32 is searched as soon as the ring holds one.
+template <int NWARP>
+__device__ __forceinline__ void open_search_ring(const uint32_t *mb, uint32_t ngroups, uint32_t wg0, uint32_t *ring,
+                                                 const uint32_t *win, const uint32_t *PR, uint32_t KW,
+                                                 unsigned long long n_lo, uint32_t ks, uint32_t i_start,
+                                                 const RangeParams &prm, SubAcc &acc, const SubShared &ss, Ctrl *ctrl)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t below = (1u << lane) - 1u;
+    uint32_t head = 0, tail = 0;                       // warp-uniform ring positions
+    uint32_t U_nx = ngroups ? mb[lane] : 0u;           // the next group's masks load ahead
+    for (uint32_t gi = 0; gi < ngroups; gi++) {
+        uint32_t U = U_nx;
+        if (gi + 1 < ngroups) U_nx = mb[32u * (gi + 1) + lane];
+        const uint32_t kw = 32u * (wg0 + 32u * NWARP * gi + lane);
+        for (;;) {
+            const uint32_t has = __ballot_sync(GB_FULL_MASK, U != 0u);
+            if (!has) break;
+            if (U) {
+                ring[(tail + __popc(has & below)) & 63u] = kw + (uint32_t)(__ffs(U) - 1);
+                U &= U - 1u;
+            }
+            tail += __popc(has);                       // at most 63 entries are pending
+            if (tail - head >= 32u) {
+                __syncwarp();
+                const uint32_t k = ring[(head + lane) & 63u];
+                __syncwarp();
+                tail_one(win, PR, KW, k, true, n_lo, ks, i_start, prm, acc, ss, ctrl);
+                head += 32u;
+            }
+        }
+    }
+    __syncwarp();
+    if (tail != head) {
+        const uint32_t k = ring[(head + lane) & 63u];
+        tail_one(win, PR, KW, k, lane < tail - head, n_lo, ks, i_start, prm, acc, ss, ctrl);
+    }
 }
 
 }  // namespace gbk
