@@ -47,7 +47,11 @@ def parse():
     ap.add_argument("--n-top", type=int, default=N_TOP)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--cpu-records", type=int, default=600)
+    ap.add_argument("--cpu-all-cores", type=int, default=100, metavar="RECORDS_PER_CORE",
+                    help="records per host core for the all-cores oracle run (0 = skip)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default configuration")
+    ap.add_argument("--option", action="append", default=[], metavar="KEY=VALUE",
+                    help="set a library option before the run (repeatable; e.g. search_chunks=6)")
     return ap.parse_args()
 
 
@@ -130,7 +134,8 @@ class ClockSampler:
 #   word statistics             100 per 32-n word (popcounts over 8 planes)
 #   per-n tail                  20 + 6 per 32-candidate chunk
 MODEL = {"mark": 4, "fill": 4, "step": 3, "word_stats": 100, "tail": 20, "tail_chunk": 6}
-PAT_PRIMES = [11, 13, 17, 19, 23, 29, 31, 37, 41, 43, 47, 53, 59, 61]
+MODEL_WHEEL = 13          # primes pre-sieved by the fill in the model
+MODEL_BOUND = 255         # bit-parallel candidates of the model: the odd primes below 256
 
 
 def odd_primes_upto(x: int):
@@ -144,39 +149,41 @@ def odd_primes_upto(x: int):
     return np.nonzero(sieve)[0][1:]
 
 
-def algorithmic_instructions(n0: int, n_total: int, tile_bits: int, k_words: int, wheel: int,
-                             pattern_max: int, search_chunks: int, p_max: int, hist) -> dict:
-    """Lane instructions the algorithm needs for one launch over n_total even n from n0.
+def algorithmic_instructions(n0: int, n_total: int, k_words: int, hist) -> dict:
+    """Lane instructions a fixed statement of the algorithm needs for n_total
+    even n from n0, independent of the kernel's tuning (tile size, pattern
+    primes, search chunks):
 
-    Marks are counted exactly per prime over [W_0, q_max] (odd multiples from
-    p^2 on); only the K - 1 overlap bits between consecutive windows are
-    added by density.  The tail size comes from the run's own histogram.
+    * fill: one word per 32 odd q in [n0 + 1 - 2K, n_last - 1], wheel 3..13;
+    * marks: every odd multiple from p^2 of every prime 13 < p <= sqrt(q_max)
+      in that q range, counted exactly;
+    * search: per word of 32 n, one bit-parallel step per odd prime below 256
+      plus the word statistics; per n with p_min above 251 (from the run's own
+      histogram), the per-n walk.
     """
     import numpy as np
-    S, K = 1 << tile_bits, 32 * k_words
-    ntiles = (n_total + S - 1) // S
+    K = 32 * k_words
     n_last = n0 + 2 * (n_total - 1)
     q_lo = max(n0 + 1 - 2 * K, 1)
     q_hi = n_last - 1
-    pat = [q for q in PAT_PRIMES if wheel < q <= pattern_max]
-    bound = max([wheel] + pat)
     primes = odd_primes_upto(int(q_hi ** 0.5) + 1).astype(np.float64)
-    primes = primes[(primes > bound) & (primes * primes <= q_hi)]
+    primes = primes[(primes > MODEL_WHEEL) & (primes * primes <= q_hi)]
     start = np.maximum(primes * primes, np.ceil(q_lo / primes) * primes)
     start = np.where(start % 2 == 0, start + primes, start)
     marks = float(np.sum(np.maximum(0.0, np.floor((q_hi - start) / (2 * primes)) + 1)))
-    marks += (ntiles - 1) * (K - 1) * float(np.sum(1.0 / primes))
-    words = n_total / 32 + ntiles
-    fill_words = (n_total + ntiles * K) / 32 + ntiles
-    bb = min(64 * search_chunks - 1, p_max) if search_chunks else 0
-    cands = [int(c) for c in odd_primes_upto(max(bb, 3)) if c <= bb]
+    words = n_total / 32
+    fill_words = (q_hi - q_lo) / 64 + 1
+    cands = [int(c) for c in odd_primes_upto(MODEL_BOUND)]
     step_cost = sum(MODEL["step"] + bin(c).count("1") for c in cands)
-    tail_n = sum(hist[b] for b in range(len(hist)) if (1 << b) > bb) if search_chunks else n_total
-    instr = (marks * MODEL["mark"] + fill_words * (MODEL["fill"] + len(pat)) + words * step_cost
-             + words * MODEL["word_stats"] * (1 if search_chunks else 0)
-             + tail_n * (MODEL["tail"] + 1.5 * MODEL["tail_chunk"]))
+    tail_n = sum(hist[b] for b in range(len(hist)) if (1 << b) > MODEL_BOUND)
+    instr = (marks * MODEL["mark"] + fill_words * MODEL["fill"] + words * step_cost
+             + words * MODEL["word_stats"] + tail_n * (MODEL["tail"] + 1.5 * MODEL["tail_chunk"]))
+    # shared-memory accesses: a read-modify-write per mark, a store per fill
+    # word, two window loads per 32-candidate chunk of a word (4 chunks), two
+    # per chunk of the per-n walk
+    smem = marks + fill_words + words * 8 + tail_n * 1.5 * 2
     return {"instr": instr, "per_n": instr / n_total, "marks_per_n": marks / n_total,
-            "tail_fraction": tail_n / n_total}
+            "smem": smem, "tail_fraction": tail_n / n_total}
 
 
 def csrc_digest() -> str:
@@ -230,6 +237,49 @@ def cpu_sample(n_top: int, count: int, seed: int = 0xB0):
     return n / dt, n, dt, len(idx)
 
 
+def _oracle_records(job):
+    """Worker of the all-cores oracle run: fold the given records."""
+    n_top, recs = job
+    import oracle
+    from paper_2603_07850_gb300 import workloads as W
+    cfg = W.RangeConfig("bench", 4, n_top + 1, P_MAX, SEG_BITS, 0, "")
+    base = oracle.primes_upto(int(n_top ** 0.5) + 2)
+    lim = int(n_top ** 0.5) + 2
+    n = 0
+    for r in recs:
+        a, b = W.record_bounds(cfg.lo, cfg.hi, SEG_BITS, r)
+        st, out, _, _ = oracle.pmin_range(a, b, p_max=P_MAX, seg_bits=SEG_BITS, base=(base, lim))
+        n += out[0].n_count
+    return n
+
+
+def cpu_sample_all_cores(n_top: int, per_core: int, seed: int = 0xB1):
+    """The same oracle, one process per host core (spawned: this process
+    already holds a CUDA context), each folding its share of seeded records."""
+    import multiprocessing as mp
+    import platform
+    from paper_2603_07850_gb300 import workloads as W
+    cores = os.cpu_count() or 1
+    cfg = W.RangeConfig("bench", 4, n_top + 1, P_MAX, SEG_BITS, 0, "")
+    idx = list(W.sample_records(cfg, per_core * cores, seed))
+    jobs = [(n_top, idx[c::cores]) for c in range(cores)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_records, [(n_top, idx[:1])] * cores)      # start-up outside the clock
+        t = time.perf_counter()
+        n = sum(pool.map(_oracle_records, jobs))
+        dt = time.perf_counter() - t
+    model = platform.processor() or platform.machine()
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return n / dt, n, dt, len(idx), cores, model
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -276,9 +326,13 @@ def run_ours(args):
     if dist:
         dist.barrier()
     gb.load()
+    unit_peaks = gb.gb_measure_peaks()          # microbenchmarks, before anything is timed
     gb.gb_init(P_MAX, SEG_BITS)
     gb.gb_set_option("time_kernel", 1)
     gb.gb_set_option("autotune", 0 if args.no_autotune else 1)   # the first warm-up step tunes
+    for kv in args.option:
+        k, v = kv.split("=", 1)
+        gb.gb_set_option(k, int(v))
     lo = rank * args.n_top + 4
     hi = (rank + 1) * args.n_top + 1
     n_total = (hi - 1 - lo) // 2 + 1 if lo % 2 == 0 else None
@@ -365,9 +419,7 @@ def run_ours(args):
     peaks = load_peaks()
     opt = {k: gb.gb_get_option(k) for k in ("k_words", "tile_bits", "wheel", "pattern_max",
                                             "search_chunks", "threads", "sms")}
-    alg = algorithmic_instructions(out["n_first"], out["n_count"], opt["tile_bits"], opt["k_words"],
-                                   opt["wheel"], opt["pattern_max"], opt["search_chunks"], P_MAX,
-                                   out["hist"])
+    alg = algorithmic_instructions(out["n_first"], out["n_count"], opt["k_words"], out["hist"])
     kus = statistics.mean(kernel_us) if kernel_us else None
     sm_clock = (peaks or {}).get("sm_max_mhz", 2070.0)
     peak = opt["sms"] * 128 * sm_clock * 1e6          # 4 schedulers x 32 lanes per SM per clock
@@ -395,7 +447,15 @@ def run_ours(args):
                      "algorithmic_instr_per_n": alg["per_n"], "marks_per_n": alg["marks_per_n"],
                      "tail_fraction": alg["tail_fraction"],
                      "peak_note": "issue slots: SMs x 4 schedulers x 32 lanes x max SM clock "
-                                  "(derived, of measured clock)"},
+                                  "(derived, of measured clock)",
+                     "measured_units": {k: v / 1e9 for k, v in unit_peaks.items() if k != "sms"},
+                     "frac_vs_measured_int": (achieved / (unit_peaks["int_logic_ops"] + unit_peaks["int_mad_ops"])
+                                              if achieved else None),
+                     "frac_vs_measured_smem": (alg["smem"] / (kus * 1e-6) / unit_peaks["smem_atomic_ops"]
+                                               if kus else None),
+                     "measured_note": "G lane-ops/s of our microbenchmarks (gb_measure_peaks): INT32 "
+                                      "logic/shift, integer mad, popc, conflict-free shared atomicAnd; the "
+                                      "integer fraction divides by logic + mad (two pipes)"},
         "plain": plain,
         "speedup_vs_plain": (tot_n / (ms * 1e-3)) / plain["value"] if plain else None,
         "result": {k: merged[k] for k in ("n_count", "max_pmin", "argmax_n", "sum_pmin", "n_slow")},
@@ -408,6 +468,15 @@ def run_ours(args):
     except Exception as e:  # noqa: BLE001
         line["cpu_baseline"] = {"value": None, "unit": "even_n/s", "cores": 1, "kind": "oracle",
                                 "sample": f"failed: {e}"}
+    if args.cpu_all_cores > 0:
+        try:
+            v, n, dt, k, cores, model = cpu_sample_all_cores(args.n_top, args.cpu_all_cores)
+            line["cpu_baseline_all_cores"] = {
+                "value": v, "unit": "even_n/s", "cores": cores, "kind": "oracle", "cpu": model,
+                "sample": f"{k} seeded records of 2^20 even n in [4, 1e12], one oracle process per "
+                          f"core, {dt:.1f} s wall"}
+        except Exception as e:  # noqa: BLE001
+            line["cpu_baseline_all_cores"] = {"value": None, "sample": f"failed: {e}"}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

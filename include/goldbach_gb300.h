@@ -107,6 +107,17 @@ typedef struct {
     uint64_t device_bytes;     /* device memory currently held by the library  */
 } gb_stats_t;
 
+/* Measured throughput of the units the verifier is bound by, in lane
+ * operations per second over the whole GPU (see gb_measure_peaks). */
+typedef struct {
+    double int_logic_ops;      /* lop3 and shf (the INT32 logic/shift path)     */
+    double int_mad_ops;        /* integer multiply-add (mad.lo.u32)             */
+    double popc_ops;           /* popc                                          */
+    double smem_atomic_ops;    /* shared-memory atomicAnd, no bank conflicts    */
+    uint32_t sms;              /* multiprocessors of the measured GPU           */
+    uint32_t reserved;
+} gb_peaks_t;
+
 /* ---- lifecycle ----------------------------------------------------------- */
 
 /*
@@ -277,6 +288,17 @@ int gb_poll(uint64_t ticket, gb_result *out, int32_t timeout_ms);
 int gb_progress(uint64_t *tiles_done, uint64_t *tiles_total);
 
 int gb_stats(gb_stats_t *out);
+
+/*
+ * gb_measure_peaks -- run the microbenchmarks behind the measured roofline on
+ * the current CUDA device: INT32 logic/shift, integer multiply-add, popcount
+ * and conflict-free shared-memory atomicAnd.  Each is a full-occupancy kernel
+ * (two 1,024-thread CTAs per SM) with eight independent chains per thread,
+ * timed with CUDA events (best of three after a warm-up launch; about 0.1 s
+ * in all).  Needs no gb_init and holds no memory afterwards.  `out` is
+ * caller-owned.  Returns GB_OK, GB_EINVAL (out is NULL) or GB_ECUDA.
+ */
+int gb_measure_peaks(gb_peaks_t *out);
 const char *gb_last_error(void);
 
 #ifdef __cplusplus

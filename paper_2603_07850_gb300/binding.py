@@ -68,6 +68,15 @@ class GbStats(ctypes.Structure):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
 
 
+class GbPeaks(ctypes.Structure):
+    _fields_ = [("int_logic_ops", ctypes.c_double), ("int_mad_ops", ctypes.c_double),
+                ("popc_ops", ctypes.c_double), ("smem_atomic_ops", ctypes.c_double),
+                ("sms", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
 class GbError(RuntimeError):
     def __init__(self, fn: str, code: int, msg: str):
         super().__init__(f"{fn} -> {code}: {msg}")
@@ -102,6 +111,7 @@ def load(path: str = LIB_PATH):
         "gb_poll": ([U64, P(GbResult), i32], ctypes.c_int),
         "gb_stats": ([P(GbStats)], ctypes.c_int),
         "gb_progress": ([P(U64), P(U64)], ctypes.c_int),
+        "gb_measure_peaks": ([P(GbPeaks)], ctypes.c_int),
         "gb_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -210,6 +220,14 @@ def gb_stats() -> dict:
     s = GbStats()
     _check("gb_stats", load().gb_stats(ctypes.byref(s)))
     return s.as_dict()
+
+
+def gb_measure_peaks() -> dict:
+    """Measured lane operations/s of INT32 logic, integer mad, popc and
+    conflict-free shared atomicAnd on the current GPU."""
+    p = GbPeaks()
+    _check("gb_measure_peaks", load().gb_measure_peaks(ctypes.byref(p)))
+    return p.as_dict()
 
 
 def result_from_bytes(raw: bytes) -> dict:
