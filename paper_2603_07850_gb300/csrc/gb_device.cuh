@@ -62,13 +62,14 @@ __device__ __forceinline__ uint32_t mod_recip(unsigned long long x, uint32_t p,
     return (uint32_t)r;
 }
 
-// floor(sqrt(x)) for any 64-bit x, exact (corrected with division).
+// floor(sqrt(x)) for any 64-bit x, exact: a double-precision estimate (off by
+// at most one) corrected with 64-bit products, never above 2^32 - 1.
 __device__ __forceinline__ unsigned long long isqrt_u64(unsigned long long x)
 {
     unsigned long long r = (unsigned long long)sqrt((double)x);
     if (r > 0xFFFFFFFFull) r = 0xFFFFFFFFull;
-    while (r > 0 && r > x / r) r--;
-    while (r < 0xFFFFFFFFull && (r + 1) <= x / (r + 1)) r++;
+    while (r > 0 && r * r > x) r--;
+    while (r < 0xFFFFFFFFull && (r + 1) * (r + 1) <= x) r++;
     return r;
 }
 
@@ -80,6 +81,25 @@ __device__ __forceinline__ uint32_t count_le(const uint32_t *primes, uint32_t n,
     while (lo < hi) {
         uint32_t mid = (lo + hi) >> 1;
         if ((unsigned long long)primes[mid] <= v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// The same count by a whole warp (every lane calls it, all get the answer):
+// each round the 32 lanes test 32 evenly spaced entries and a ballot narrows
+// the range 32-fold, so a 2^20-prime table takes four dependent loads.
+__device__ __forceinline__ uint32_t count_le_warp(const uint32_t *primes, uint32_t n, unsigned long long v)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    uint32_t lo = 0, hi = n;                             // the count lies in [lo, hi]
+    while (lo < hi) {
+        const uint32_t step = (hi - lo + 31) / 32;
+        const uint32_t idx = lo + (lane + 1) * step - 1;
+        const bool le = idx < hi && (unsigned long long)primes[idx] <= v;
+        const uint32_t cnt = __popc(__ballot_sync(GB_FULL_MASK, le));
+        const uint32_t nhi = lo + (cnt + 1) * step - 1;
+        lo += cnt * step;
+        hi = nhi < hi ? nhi : hi;
     }
     return lo;
 }
@@ -512,7 +532,7 @@ __device__ __forceinline__ void build_window(uint32_t *win, const uint32_t *wpat
 {
     fill_pass<WHEEL, NT>(win, wpat, g, t.pat_lo, t.pat_hi, t.groups);
     __syncthreads();
-    uint32_t np = count_le(t.primes, t.nprimes, isqrt_u64(g.q_hi));
+    uint32_t np = count_le_warp(t.primes, t.nprimes, isqrt_u64(g.q_hi));
     if (np > np_cap) np = np_cap;
     mark_pass<NT>(win, g, t, np);
     if (ent) bucket_pass<NT>(win, g, ent, b0, b1, ctrl);

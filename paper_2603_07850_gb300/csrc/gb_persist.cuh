@@ -214,8 +214,9 @@ __device__ __forceinline__ void run_tile(const RangeParams &prm, unsigned long l
                 gi = gmax;
             }
             __syncwarp();
-            open_search_ring<NWARP>(mb, gi, wbeg + 32u * warp, &s.ring[warp][0], win, PR, KW, n_lo, ks, i_start,
-                                    prm, acc, ss, ctrl);
+            OpenRing rg{&s.ring[warp][0], 0u, 0u};
+            ring_groups<NWARP>(rg, mb, 0u, gi, wbeg + 32u * warp, win, PR, KW, n_lo, ks, i_start, prm, acc, ss, ctrl);
+            ring_flush(rg, win, PR, KW, n_lo, ks, i_start, prm, acc, ss, ctrl);
             a.mx = acc.mx;
             a.arg = acc.mx ? kr0 + acc.arg : ~0ull;
             a.sum = acc.sum;

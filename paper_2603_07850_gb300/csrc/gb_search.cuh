@@ -190,26 +190,37 @@ __device__ __forceinline__ uint32_t bulk_word(const uint32_t *win, uint32_t w, u
 {
     // Every candidate is odd, so plane 0 collects exactly the resolved bits:
     // it doubles as the "already resolved" mask (invalid bits start set).
+    // The candidates of one 32-wide range of p share the bits of p from bit 5
+    // up, so planes 5.. take the bits the range resolved once, after it; each
+    // candidate adds its newly resolved bits only to planes 1..4.
     uint32_t B0 = ~valid, B1 = 0, B2 = 0, B3 = 0, B4 = 0, B5 = 0, B6 = 0, B7 = 0, B8 = 0;
 #pragma unroll
     for (int c = 0; c < BC; c++) {
         const uint32_t lo = win[w + KW - 1 - c], hi = win[w + KW - c];
 #pragma unroll
-        for (int ci = 0; ci < cand_count(BC); ci++) {
-            const uint32_t p = cand_prime(ci);
-            const uint32_t i = (p - 1) >> 1;
-            if ((int)(i >> 5) == c && (ALL || p <= bb)) {
-                const uint32_t x = __funnelshift_r(lo, hi, 31u - (i & 31u));
-                const uint32_t nw = x & ~B0;            // newly resolved: plane j gets them
-                if (p & 2u) B1 = nw * one + B1;
-                if (p & 4u) B2 = nw * one + B2;
-                if (p & 8u) B3 = nw * one + B3;
-                if (p & 16u) B4 = nw * one + B4;
-                if (p & 32u) B5 = nw * one + B5;
-                if (p & 64u) B6 = nw * one + B6;
-                if (p & 128u) B7 = nw * one + B7;
-                if (p & 256u) B8 = nw * one + B8;
-                B0 |= x;
+        for (int h = 0; h < 2; h++) {
+            const uint32_t g = 2u * c + h;                // p in [32 g, 32 g + 32)
+            const uint32_t B_start = B0;
+#pragma unroll
+            for (int ci = 0; ci < cand_count(BC); ci++) {
+                const uint32_t p = cand_prime(ci);
+                const uint32_t i = (p - 1) >> 1;
+                if ((p >> 5) == g && (ALL || p <= bb)) {
+                    const uint32_t x = __funnelshift_r(lo, hi, 31u - (i & 31u));
+                    const uint32_t nw = x & ~B0;        // newly resolved
+                    if (p & 2u) B1 = nw * one + B1;
+                    if (p & 4u) B2 = nw * one + B2;
+                    if (p & 8u) B3 = nw * one + B3;
+                    if (p & 16u) B4 = nw * one + B4;
+                    B0 |= x;
+                }
+            }
+            if (g != 0u) {
+                const uint32_t D = B0 & ~B_start;       // resolved by this range
+                if ((32u * g) & 32u) B5 = D * one + B5;
+                if ((32u * g) & 64u) B6 = D * one + B6;
+                if ((32u * g) & 128u) B7 = D * one + B7;
+                if ((32u * g) & 256u) B8 = D * one + B8;
             }
         }
     }
@@ -388,42 +399,58 @@ __device__ __forceinline__ void open_search(const uint32_t *mb, uint32_t ngroups
 // hands over the lowest open bit of its word, its slot in the warp's 64-entry
 // shared ring given by a ballot and a popcount (about three steps per group at
 // 10^12), and a full round of 32 is searched as soon as the ring holds one.
+struct OpenRing {
+    uint32_t *q;
+    uint32_t head, tail;                               // warp-uniform positions
+};
+
+// Groups [g0, g1) of the warp's open masks mb (lane l of group gi at
+// mb[32 gi + l], word wg0 + 32 NWARP gi + l).
 template <int NWARP>
-__device__ __forceinline__ void open_search_ring(const uint32_t *mb, uint32_t ngroups, uint32_t wg0, uint32_t *ring,
-                                                 const uint32_t *win, const uint32_t *PR, uint32_t KW,
-                                                 unsigned long long n_lo, uint32_t ks, uint32_t i_start,
-                                                 const RangeParams &prm, SubAcc &acc, const SubShared &ss, Ctrl *ctrl)
+__device__ __forceinline__ void ring_groups(OpenRing &rg, const uint32_t *mb, uint32_t g0, uint32_t g1, uint32_t wg0,
+                                            const uint32_t *win, const uint32_t *PR, uint32_t KW,
+                                            unsigned long long n_lo, uint32_t ks, uint32_t i_start,
+                                            const RangeParams &prm, SubAcc &acc, const SubShared &ss, Ctrl *ctrl)
 {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t below = (1u << lane) - 1u;
-    uint32_t head = 0, tail = 0;                       // warp-uniform ring positions
-    uint32_t U_nx = ngroups ? mb[lane] : 0u;           // the next group's masks load ahead
-    for (uint32_t gi = 0; gi < ngroups; gi++) {
+    uint32_t U_nx = g0 < g1 ? mb[32u * g0 + lane] : 0u; // the next group's masks load ahead
+    for (uint32_t gi = g0; gi < g1; gi++) {
         uint32_t U = U_nx;
-        if (gi + 1 < ngroups) U_nx = mb[32u * (gi + 1) + lane];
+        if (gi + 1 < g1) U_nx = mb[32u * (gi + 1) + lane];
         const uint32_t kw = 32u * (wg0 + 32u * NWARP * gi + lane);
         for (;;) {
             const uint32_t has = __ballot_sync(GB_FULL_MASK, U != 0u);
             if (!has) break;
             if (U) {
-                ring[(tail + __popc(has & below)) & 63u] = kw + (uint32_t)(__ffs(U) - 1);
+                rg.q[(rg.tail + __popc(has & below)) & 63u] = kw + (uint32_t)(__ffs(U) - 1);
                 U &= U - 1u;
             }
-            tail += __popc(has);                       // at most 63 entries are pending
-            if (tail - head >= 32u) {
+            rg.tail += __popc(has);                    // at most 63 entries are pending
+            if (rg.tail - rg.head >= 32u) {
                 __syncwarp();
-                const uint32_t k = ring[(head + lane) & 63u];
+                const uint32_t k = rg.q[(rg.head + lane) & 63u];
                 __syncwarp();
                 tail_one(win, PR, KW, k, true, n_lo, ks, i_start, prm, acc, ss, ctrl);
-                head += 32u;
+                rg.head += 32u;
             }
         }
     }
+}
+
+// Search the entries still in the ring (fewer than 32).
+__device__ __forceinline__ void ring_flush(OpenRing &rg, const uint32_t *win, const uint32_t *PR, uint32_t KW,
+                                           unsigned long long n_lo, uint32_t ks, uint32_t i_start,
+                                           const RangeParams &prm, SubAcc &acc, const SubShared &ss, Ctrl *ctrl)
+{
+    const uint32_t lane = threadIdx.x & 31;
     __syncwarp();
-    if (tail != head) {
-        const uint32_t k = ring[(head + lane) & 63u];
-        tail_one(win, PR, KW, k, lane < tail - head, n_lo, ks, i_start, prm, acc, ss, ctrl);
+    if (rg.tail != rg.head) {
+        const uint32_t k = rg.q[(rg.head + lane) & 63u];
+        tail_one(win, PR, KW, k, lane < rg.tail - rg.head, n_lo, ks, i_start, prm, acc, ss, ctrl);
     }
+    __syncwarp();
+    rg.head = rg.tail = 0;
 }
 
 }  // namespace gbk
