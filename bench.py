@@ -435,6 +435,9 @@ def run_ours(args):
                    "tile_bits": gb.gb_get_option("tile_bits"),
                    "threads": gb.gb_get_option("threads"), "wheel": gb.gb_get_option("wheel"),
                    "search_chunks": gb.gb_get_option("search_chunks"),
+                   "pattern_max": gb.gb_get_option("pattern_max"),
+                   "search_pmax": gb.gb_get_option("search_pmax"),
+                   "tier_b_min": gb.gb_get_option("tier_b_min"),
                    "l2": "flushed between steps (512 MB write)", "form": "persistent"},
         "e2e": {"value": tot_n / e2e_s, "unit": "even_n/s", "h2d_bytes_per_step": 64,
                 "d2h_bytes_per_step": gb.RESULT_BYTES},

@@ -167,7 +167,7 @@ int gb_init(uint32_t p_max, uint32_t seg_bits);
  *                   n with p_min above it take the slow path, but n_slow and
  *                   every other output still refer to P_max
  *   "bucket_min"    smallest base prime handled by the bucket pre-pass,
- *                   0 = the window span (default), else >= 64
+ *                   0 = four window spans, 4 (S + K) (default), else 64 .. 2^28
  *   "bucket_chunk_tiles" tiles per bucket pre-pass chunk, 1..8192 (default 2048)
  * Returns GB_OK or GB_EINVAL (unknown key or value out of range).
  */

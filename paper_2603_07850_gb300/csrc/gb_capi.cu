@@ -51,7 +51,7 @@ struct Options {
     int64_t timeout_ms = 600000;
     int64_t serve_batch_tiles = 1024;
     int64_t time_kernel = 0;       // record CUDA events around the persistent kernel
-    int64_t bucket_min = 0;        // smallest bucketed prime; 0 = the window span S + K
+    int64_t bucket_min = 0;        // smallest bucketed prime; 0 = four window spans 4 (S + K)
     int64_t bucket_chunk_tiles = 2048;
     int64_t search_pmax = 0;       // window search bound; 0 = P_max
     int64_t search_chunks = 4;     // bit-parallel search over p < 64 * this (0 = per-n search)
@@ -521,7 +521,10 @@ int enqueue_persistent(cudaStream_t st, const CallPlan &cp, gb_result *dev_out, 
 uint64_t bucket_bound()
 {
     if (g.opt.bucket_min > 0) return (uint64_t)g.opt.bucket_min;
-    return (1ull << g.opt.tile_bits) + 32ull * g.k_words;
+    // four window spans: measured on GB300 at 1e13, 1e15 and 1e18 against
+    // one, two, 16 and 64 spans; below it the lane-per-prime crossing-off
+    // costs less than a bucket entry (two enumerations and a scattered store)
+    return 4ull * ((1ull << g.opt.tile_bits) + 32ull * g.k_words);
 }
 
 uint32_t count_odd_primes_below(uint64_t x)
@@ -546,15 +549,39 @@ bool needs_buckets(const CallPlan &cp)
     return isqrt_host(n_last) >= bucket_bound();
 }
 
+// Upper bound on the bucket entries of one chunk, found without the device:
+// a bucket prime p (B <= p <= P) has at most span/p + 1 hits in the chunk's
+// `span` window bits (its odd multiples are p bits apart), and each hit is
+// entered in at most `dup` overlapping windows.  The sum of 1/p is exact over
+// the host's primes up to 2^16; above, Rosser and Schoenfeld's bounds on
+// sum_{p <= x} 1/p (within 1/(2 ln^2 x) of ln ln x + M for x >= 286) give
+// sum_{lo < p <= P} 1/p < ln ln P - ln ln lo + 1/ln^2 lo.
+uint64_t bucket_entries_bound(uint64_t B, uint64_t P, uint64_t nprimes, uint64_t span, uint64_t dup)
+{
+    double rs = 0.0;
+    for (uint32_t q : g.h_small)
+        if (q >= B && q <= P) rs += 1.0 / q;
+    const double lo = std::max<double>((double)B, 65536.0);
+    if ((double)P > lo) {
+        const double l = std::log(lo);
+        rs += std::log(std::log((double)P)) - std::log(l) + 1.0 / (l * l);
+    }
+    const double e = (double)dup * ((double)span * rs + (double)nprimes) + 1024.0;
+    return (uint64_t)std::ceil(e * 1.01);
+}
+
 // Persistent pipeline with the large primes bucketed: tiles are processed in
 // chunks; per chunk the pre-pass counts, scans and fills the buckets, then
-// the persistent kernel sieves the chunk's tiles.
+// the persistent kernel sieves the chunk's tiles.  The entry buffer is sized
+// once from bucket_entries_bound, so the chunks are enqueued back to back
+// with no host round trip (a fill that would pass the bound sets F_INTERNAL
+// instead of writing).
 int run_persistent_buckets(const CallPlan &cp, int grid, size_t smem, int mg, gb_result *dev_out,
                            cudaStream_t st, bool sync_result)
 {
     int rc;
     const uint64_t B = bucket_bound();
-    if (B > (1ull << 22)) { set_error("bucket_min above 2^22 is not supported"); return GB_EINVAL; }
+    if (B > (1ull << 28)) { set_error("bucket_min above 2^28 is not supported"); return GB_EINVAL; }
     const uint32_t i0 = count_odd_primes_below(B);
     const uint64_t CT = (uint64_t)g.opt.bucket_chunk_tiles;
     if (g.bk_tiles_cap < CT + 1) {
@@ -574,25 +601,24 @@ int run_persistent_buckets(const CallPlan &cp, int grid, size_t smem, int mg, gb
     const int clear_records = g.opt.tile_bits < g.seg_bits ? 1 : 0;
     CK(launch_set_params(st, g.d_params, p));
     CK(launch_clear(st, g.d_params, g.d_recs, g.d_ctrl, clear_records, clear_records ? 4 * g.sms : 1));
+    const uint64_t S = 1ull << g.opt.tile_bits, K = 32ull * g.k_words;
+    const uint64_t P = isqrt_host(cp.n0 + 2 * (cp.n_total - 1));
+    const uint64_t cap = bucket_entries_bound(B, P, g.nprimes - i0, CT * S + K, 1 + (K - 1 + S - 1) / S);
+    if (cap >= (1ull << 32)) { set_error("bucket chunk too large: lower bucket_chunk_tiles"); return GB_ENOMEM; }
+    if (cap > g.bk_ent_cap) {
+        dev_free(&g.d_bk_ent, 4 * g.bk_ent_cap);
+        g.bk_ent_cap = 0;
+        if ((rc = dev_alloc(&g.d_bk_ent, 4 * cap))) return rc;
+        g.bk_ent_cap = cap;
+    }
     uint64_t launches = 2;
     for (uint64_t t0 = 0; t0 < cp.ntiles; t0 += CT) {
         const uint32_t nt = (uint32_t)std::min<uint64_t>(CT, cp.ntiles - t0);
         CK(cudaMemsetAsync(g.d_bk_counts, 0, 4ull * nt, st));
         CK(launch_bucket_prepass(st, 4 * g.sms, g.d_params, t, i0, t0, nt, g.d_bk_counts, g.d_bk_off,
-                                 g.d_bk_cursor, nullptr, 0));
-        unsigned long long total = 0;
-        CK(cudaMemcpyAsync(&total, g.d_bk_off + nt, 8, cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        if (total >= (1ull << 32)) { set_error("bucket chunk too large: lower bucket_chunk_tiles"); return GB_ENOMEM; }
-        if (total > g.bk_ent_cap) {
-            dev_free(&g.d_bk_ent, 4 * g.bk_ent_cap);
-            g.bk_ent_cap = 0;
-            size_t cap = (size_t)(total + total / 8 + 1024);
-            if ((rc = dev_alloc(&g.d_bk_ent, 4 * cap))) return rc;
-            g.bk_ent_cap = cap;
-        }
+                                 g.d_bk_cursor, nullptr, 0, 0, nullptr));
         CK(launch_bucket_prepass(st, 4 * g.sms, g.d_params, t, i0, t0, nt, g.d_bk_counts, g.d_bk_off,
-                                 g.d_bk_cursor, g.d_bk_ent, 1));
+                                 g.d_bk_cursor, g.d_bk_ent, 1, g.bk_ent_cap, g.d_ctrl));
         p.tile0 = t0;
         p.tile_end = t0 + nt;
         p.bk_off = g.d_bk_off;
@@ -1056,7 +1082,7 @@ const OptDesc kOpts[] = {
     {"timeout_ms", &Options::timeout_ms, 1, 1ll << 40},
     {"serve_batch_tiles", &Options::serve_batch_tiles, 1, 1 << 24},
     {"time_kernel", &Options::time_kernel, 0, 1},
-    {"bucket_min", &Options::bucket_min, 0, 1 << 22},
+    {"bucket_min", &Options::bucket_min, 0, 1 << 28},
     {"bucket_chunk_tiles", &Options::bucket_chunk_tiles, 1, 8192},
     {"search_pmax", &Options::search_pmax, 0, 1 << 20},
     {"search_chunks", &Options::search_chunks, 0, 8},
@@ -1266,13 +1292,13 @@ int ctx_serve_init_slot(int slot, const ServePlan &sp, uint64_t *bucket_bytes)
     CK(cudaMallocAsync((void **)&off, 8ull * (nt + 1), sv.pp));
     CK(cudaMemsetAsync(sv.d_cnt, 0, 4ull * nt, sv.pp));
     CK(launch_bucket_prepass(sv.pp, 4 * g.sms, &sv.d_slots[slot].prm, t, h.prm.bk_prime0, 0, nt, sv.d_cnt,
-                             off, sv.d_cur, nullptr, 0));
+                             off, sv.d_cur, nullptr, 0, 0, nullptr));
     CK(cudaMemcpyAsync(sv.h_total, off + nt, 8, cudaMemcpyDeviceToHost, sv.pp));
     CK(cudaStreamSynchronize(sv.pp));
     const unsigned long long total = *sv.h_total;
     CK(cudaMallocAsync((void **)&ent, 4ull * total + 16, sv.pp));
     CK(launch_bucket_prepass(sv.pp, 4 * g.sms, &sv.d_slots[slot].prm, t, h.prm.bk_prime0, 0, nt, sv.d_cnt,
-                             off, sv.d_cur, ent, 1));
+                             off, sv.d_cur, ent, 1, total, sv.d_ctrl));
     h.prm.bk_off = off;
     h.prm.bk_ent = ent;
     CK(cudaMemcpyAsync(&sv.d_slots[slot].prm, &h.prm, sizeof h.prm, cudaMemcpyHostToDevice, sv.pp));

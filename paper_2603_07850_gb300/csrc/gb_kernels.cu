@@ -437,7 +437,8 @@ bucket_count_kernel(const RangeParams *__restrict__ prm_g, Tables t, uint32_t i0
 template <int NT>
 __global__ void __launch_bounds__(NT)
 bucket_fill_kernel(const RangeParams *__restrict__ prm_g, Tables t, uint32_t i0, unsigned long long t0,
-                   uint32_t nt, unsigned int *__restrict__ cursor, uint32_t *__restrict__ ent)
+                   uint32_t nt, unsigned int *__restrict__ cursor, uint32_t *__restrict__ ent,
+                   unsigned long long cap, Ctrl *ctrl)
 {
     extern __shared__ unsigned int h[];
     const RangeParams prm = *prm_g;
@@ -454,7 +455,9 @@ bucket_fill_kernel(const RangeParams *__restrict__ prm_g, Tables t, uint32_t i0,
     __syncthreads();
     for (uint32_t i = i0 + blockIdx.x * NT + threadIdx.x; i < i1; i += gridDim.x * NT)
         for_each_hit(c, t.primes[i], t.recip[i], [&](uint32_t tt, uint32_t j) {
-            ent[atomicAdd(&h[tt], 1u)] = j;
+            const unsigned int e = atomicAdd(&h[tt], 1u);
+            if (e < cap) ent[e] = j;
+            else atomicOr(&ctrl->flags, F_INTERNAL);      // the host's capacity bound failed
         });
 }
 
@@ -483,14 +486,15 @@ __global__ void set_params_kernel(RangeParams *dst, RangeParams p)
 
 cudaError_t launch_bucket_prepass(cudaStream_t st, int grid, const RangeParams *prm, const Tables &t,
                                   uint32_t i0, unsigned long long t0, uint32_t nt, unsigned int *counts,
-                                  unsigned long long *off, unsigned int *cursor, uint32_t *ent, int phase)
+                                  unsigned long long *off, unsigned int *cursor, uint32_t *ent, int phase,
+                                  unsigned long long cap, Ctrl *ctrl)
 {
     const size_t smem = 4ull * nt;
     if (phase == 0) {
         bucket_count_kernel<256><<<grid, 256, smem, st>>>(prm, t, i0, t0, nt, counts);
         if (cudaPeekAtLastError() == cudaSuccess) bucket_scan_kernel<<<1, 32, 0, st>>>(counts, nt, off, cursor);
     } else {
-        bucket_fill_kernel<256><<<grid, 256, smem, st>>>(prm, t, i0, t0, nt, cursor, ent);
+        bucket_fill_kernel<256><<<grid, 256, smem, st>>>(prm, t, i0, t0, nt, cursor, ent, cap, ctrl);
     }
     return cudaGetLastError();
 }

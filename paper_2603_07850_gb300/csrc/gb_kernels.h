@@ -53,5 +53,6 @@ cudaError_t launch_set_params(cudaStream_t st, RangeParams *dst, const RangePara
 // phase 0: count hits per tile + scan into off/cursor; phase 1: fill entries
 cudaError_t launch_bucket_prepass(cudaStream_t st, int grid, const RangeParams *prm, const Tables &t,
                                   uint32_t i0, unsigned long long t0, uint32_t nt, unsigned int *counts,
-                                  unsigned long long *off, unsigned int *cursor, uint32_t *ent, int phase);
+                                  unsigned long long *off, unsigned int *cursor, uint32_t *ent, int phase,
+                                  unsigned long long cap, Ctrl *ctrl);
 }
