@@ -1179,7 +1179,7 @@ int ctx_serve_begin(int max_slots, int max_items)
     sv.nt = (int)g.opt.threads;
     int wheel = (int)g.opt.wheel, bc = (int)g.opt.search_chunks;
     sv.fn = serve_kernel_ptr(wheel, sv.nt, bc);
-    if (!sv.fn) { sv.nt = 1024; bc = 8; sv.fn = serve_kernel_ptr(13, 1024, 8); }
+    if (!sv.fn) { sv.nt = 1024; bc = 6; sv.fn = serve_kernel_ptr(13, 1024, 6); }
     sv.smem = persistent_smem((uint32_t)g.opt.tile_bits);
     if ((rc = occupancy_grid(sv.fn, sv.nt, sv.smem, &sv.grid))) return rc;
     if (bc != 0) {                                   // the bit-parallel search needs slots

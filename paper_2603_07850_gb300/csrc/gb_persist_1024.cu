@@ -26,6 +26,8 @@ const void *persistent_ptr_1024(int wheel, int bc)
 const void *serve_ptr_1024(int wheel, int bc)
 {
     if (wheel == 13 && bc == 8) return (const void *)serve_kernel<13, 1024, 8>;
+    if (wheel == 13 && bc == 6) return (const void *)serve_kernel<13, 1024, 6>;
+    if (wheel == 13 && bc == 4) return (const void *)serve_kernel<13, 1024, 4>;
     if (wheel == 13 && bc == 0) return (const void *)serve_kernel<13, 1024, 0>;
     return nullptr;
 }
