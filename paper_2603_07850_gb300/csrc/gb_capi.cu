@@ -20,6 +20,7 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <queue>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -65,11 +66,14 @@ struct GraphKey {
     const void *recs = nullptr;
     const void *olist = nullptr;
     uint32_t olist_wcap = 0, olist_ctas = 0;
+    const void *aperm = nullptr;
+    uint32_t aperm_len = 0;
     bool operator==(const GraphKey &o) const
     {
         return fn == o.fn && grid == o.grid && nt == o.nt && wheel == o.wheel &&
                merge_grid == o.merge_grid && clear_records == o.clear_records && smem == o.smem &&
-               recs == o.recs && olist == o.olist && olist_wcap == o.olist_wcap && olist_ctas == o.olist_ctas;
+               recs == o.recs && olist == o.olist && olist_wcap == o.olist_wcap && olist_ctas == o.olist_ctas &&
+               aperm == o.aperm && aperm_len == o.aperm_len;
     }
 };
 
@@ -116,6 +120,10 @@ struct Ctx {
     uint32_t *d_olist = nullptr;
     size_t olist_cap = 0;
     uint32_t olist_wcap = 0, olist_ctas = 0;
+    // balanced order of the tier-A primes (see Tables::aperm) and what it was built for
+    uint32_t *d_aperm = nullptr;
+    uint32_t aperm_len = 0;
+    uint64_t aperm_key[5] = {0, 0, 0, 0, 0};
     std::map<uint64_t, uint32_t> odd_primes_below;  // cache: bound -> #odd primes below it
     char dev_name[256] = {0};
     struct TuneCfg { int64_t tile_bits, threads, search_chunks, pattern_max, search_pmax, tier_b_min; };
@@ -279,6 +287,9 @@ Tables make_tables()
     t.olist = g.d_olist;
     t.olist_wcap = g.olist_wcap;
     t.olist_ctas = g.olist_ctas;
+    const bool aperm_fits = g.d_aperm && g.aperm_key[0] == t.iA0 && g.aperm_key[1] == t.iB0;
+    t.aperm = aperm_fits ? g.d_aperm : nullptr;
+    t.aperm_len = aperm_fits ? g.aperm_len : 0u;
     return t;
 }
 
@@ -481,10 +492,55 @@ int ensure_olist(int grid, int nt)
     return GB_OK;
 }
 
-// Grid of a persistent launch on the context's stream, with its list.
+// The tier-A primes of the current tables spread over the warps of an
+// nt-thread CTA by longest processing time first: each prime, heaviest first,
+// goes to the least-loaded warp.  A prime's load is its crossing-off steps per
+// lane, (S + K) / 32 / p, plus 16 for its first-multiple setup.  The marks
+// are exact with any order; this only evens out the warps' work.
+int ensure_aperm(int nt)
+{
+    const Tables t = make_tables();
+    const uint64_t nwarp = (uint64_t)nt / 32;
+    const uint64_t key[5] = {t.iA0, t.iB0, nwarp, (uint64_t)g.opt.tile_bits, g.k_words};
+    if (g.d_aperm && std::equal(key, key + 5, g.aperm_key)) return GB_OK;
+    dev_free(&g.d_aperm, 4ull * g.aperm_len);
+    g.aperm_len = 0;
+    std::fill(g.aperm_key, g.aperm_key + 5, 0ull);
+    const uint32_t n = t.iB0 > t.iA0 ? t.iB0 - t.iA0 : 0u;
+    if (n == 0 || t.iB0 > g.h_small.size()) return GB_OK;
+    const double span_words = ((double)(1ull << g.opt.tile_bits) + 32.0 * g.k_words) / 32.0;
+    std::vector<std::pair<double, uint32_t>> items(n);
+    for (uint32_t i = 0; i < n; i++) items[i] = {span_words / g.h_small[t.iA0 + i] + 16.0, t.iA0 + i};
+    std::sort(items.begin(), items.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
+    std::vector<std::vector<uint32_t>> lists(nwarp);
+    std::priority_queue<std::pair<double, uint64_t>, std::vector<std::pair<double, uint64_t>>,
+                        std::greater<std::pair<double, uint64_t>>> load;
+    for (uint64_t w = 0; w < nwarp; w++) load.push({0.0, w});
+    for (const auto &it : items) {
+        auto top = load.top();
+        load.pop();
+        lists[top.second].push_back(it.second);
+        load.push({top.first + it.first, top.second});
+    }
+    size_t len = 0;
+    for (const auto &l : lists) len = std::max(len, l.size());
+    std::vector<uint32_t> perm(nwarp * len, 0xffffffffu);
+    for (uint64_t w = 0; w < nwarp; w++)
+        for (size_t k = 0; k < lists[w].size(); k++) perm[w + nwarp * k] = lists[w][k];
+    int rc;
+    if ((rc = dev_alloc(&g.d_aperm, 4ull * perm.size()))) return rc;
+    CK(cudaMemcpy(g.d_aperm, perm.data(), 4ull * perm.size(), cudaMemcpyHostToDevice));
+    g.aperm_len = (uint32_t)perm.size();
+    std::copy(key, key + 5, g.aperm_key);
+    return GB_OK;
+}
+
+// Grid of a persistent launch on the context's stream, with its list and the
+// tier-A order for its thread count.
 int ctx_grid(const void *fn, int nt, size_t smem, int *grid)
 {
     int rc = occupancy_grid(fn, nt, smem, grid);
+    if (!rc) rc = ensure_aperm(nt);
     return rc ? rc : ensure_olist(*grid, nt);
 }
 
@@ -807,6 +863,8 @@ int run_persistent(uint64_t lo, uint64_t hi, CallPlan &cp)
         key.fn = fn; key.grid = grid; key.nt = nt; key.wheel = (int)g.opt.wheel; key.merge_grid = mg;
         key.clear_records = clear_records; key.smem = smem; key.recs = g.d_recs;
         key.olist = g.d_olist; key.olist_wcap = g.olist_wcap; key.olist_ctas = g.olist_ctas;
+        const Tables tk = make_tables();
+        key.aperm = tk.aperm; key.aperm_len = tk.aperm_len;
         if (!(key == g.gkey) || !g.gexec) {
             if (g.gexec) { cudaGraphExecDestroy(g.gexec); g.gexec = nullptr; }
             cudaGraph_t graph = nullptr;
@@ -967,6 +1025,7 @@ void release_all()
     dev_free(&g.d_bk_off, 8 * g.bk_tiles_cap);
     dev_free(&g.d_bk_ent, 4 * g.bk_ent_cap);
     dev_free(&g.d_olist, 4 * g.olist_cap);
+    dev_free(&g.d_aperm, 4ull * g.aperm_len);
     if (g.h_params) cudaFreeHost(g.h_params);
     if (g.h_result) cudaFreeHost(g.h_result);
     if (g.h_flags) cudaFreeHost(g.h_flags);

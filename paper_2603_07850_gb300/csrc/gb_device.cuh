@@ -436,15 +436,20 @@ __device__ __forceinline__ void mark_pass(uint32_t *win, const WinGeom &g, const
     // tier A: one warp per prime, lane l clears multiples l, l+32, ... of it.
     // A lane's step, 32 p bits, is exactly p words, so its bit position and
     // clear mask stay fixed and each mark is one atomicAnd plus an add.  Warp
-    // w takes the primes w, w + NWARP, w + 2 NWARP, ... (the dense small ones
-    // spread over all warps), 32 at a time: lane q finds the first multiple
-    // of the q-th, then the warp marks the 32 primes in turn.
+    // w takes every NWARP-th entry of the prime order (balanced by the host,
+    // else the ascending primes), 32 at a time: lane q finds the first
+    // multiple of the q-th, then the warp marks the 32 primes in turn.
     const uint32_t a_end = t.iB0 < np ? t.iB0 : np;
-    for (uint32_t i0 = t.iA0 + warp; i0 < a_end; i0 += 32u * NWARP) {
-        const uint32_t iq = i0 + lane * NWARP;
-        const uint32_t pq = iq < a_end ? t.primes[iq] : 0u;
-        const uint32_t jq = iq < a_end ? first_bit(g, pq, t.recip[iq]) : 0xffffffffu;
-        const uint32_t nq = (a_end - i0 + NWARP - 1) / NWARP;   // primes of this batch
+    // batch entry e of this warp (lane q holds entry e0 + q NWARP): a prime
+    // index, from the balanced order when the host provides one
+    const uint32_t e_beg = t.aperm ? 0u : t.iA0, e_end = t.aperm ? t.aperm_len : a_end;
+    for (uint32_t e0 = e_beg + warp; e0 < e_end; e0 += 32u * NWARP) {
+        const uint32_t e = e0 + lane * NWARP;
+        const uint32_t iq = e < e_end ? (t.aperm ? t.aperm[e] : e) : 0xffffffffu;
+        const bool in = iq < a_end;
+        const uint32_t pq = in ? t.primes[iq] : 0u;
+        const uint32_t jq = in ? first_bit(g, pq, t.recip[iq]) : 0xffffffffu;
+        const uint32_t nq = (e_end - e0 + NWARP - 1) / NWARP;   // entries of this batch
         for (uint32_t q = 0; q < nq && q < 32u; q++) {
             const uint32_t j0 = __shfl_sync(GB_FULL_MASK, jq, q);
             if (j0 == 0xffffffffu) continue;

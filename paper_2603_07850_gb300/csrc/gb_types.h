@@ -83,6 +83,11 @@ struct Tables {
     // kernels must provide it for CTAs c < olist_ctas = the grid
     uint32_t *olist;
     uint32_t olist_wcap, olist_ctas;
+    // order of the tier-A primes over the warps: warp w takes the prime
+    // indices aperm[w], aperm[w + warps_per_cta], ... (0xffffffff = none),
+    // balanced by work; null = round-robin over the ascending primes
+    const uint32_t *aperm;
+    uint32_t aperm_len;
 };
 
 }  // namespace gbk
