@@ -323,80 +323,10 @@ __device__ __forceinline__ void tail_one(const uint32_t *win, const uint32_t *PR
     }
 }
 
-// Position of the r-th (0-based) set bit of x; x has more than r set bits.
-__device__ __forceinline__ uint32_t select_bit(uint32_t x, uint32_t r)
-{
-    uint32_t pos = 0;
-#pragma unroll
-    for (uint32_t w = 16; w > 0; w >>= 1) {
-        const uint32_t c = __popc((x >> pos) & ((1u << w) - 1u));
-        if (r >= c) { r -= c; pos += w; }
-    }
-    return pos;
-}
-
 // The per-n phase of one sub-record for one warp.  During the bulk phase the
-// warp stored the open mask of each of its words (lane l of group gi at
-// mb[32 gi + l], word wg0 + 32 NWARP gi + l); here the open n are gathered
-// group by group -- lane g takes the g-th open bit of the group (a prefix
-// scan of the lanes' counts, a binary search over it, the rank-th set bit of
-// that word) -- into a 32-entry queue held one entry per lane, and every full
-// queue is searched by tail_one.  No loop here diverges with the data except
-// tail_one's own candidate walk.
-template <int NWARP>
-__device__ __forceinline__ void open_search(const uint32_t *mb, uint32_t ngroups, uint32_t wg0,
-                                            const uint32_t *win, const uint32_t *PR, uint32_t KW,
-                                            unsigned long long n_lo, uint32_t ks, uint32_t i_start,
-                                            const RangeParams &prm, SubAcc &acc, const SubShared &ss, Ctrl *ctrl)
-{
-    const uint32_t lane = threadIdx.x & 31;
-    uint32_t kq = ks, c = 0;                           // lanes < c hold a queued n (warp-uniform c)
-    uint32_t U_nx = ngroups ? mb[lane] : 0u;           // the next group's masks load ahead
-    for (uint32_t gi = 0; gi < ngroups; gi++) {
-        const uint32_t U = U_nx;
-        if (gi + 1 < ngroups) U_nx = mb[32u * (gi + 1) + lane];
-        const uint32_t cnt = __popc(U);
-        uint32_t incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(GB_FULL_MASK, incl, o);
-            if (lane >= (uint32_t)o) incl += y;
-        }
-        const uint32_t total = __shfl_sync(GB_FULL_MASK, incl, 31);
-        const uint32_t excl = incl - cnt;
-        const uint32_t wg = wg0 + 32u * NWARP * gi;
-        for (uint32_t r = 0; r < total; r += 32) {
-            const uint32_t m = total - r < 32u ? total - r : 32u;
-            const uint32_t g = r + lane;
-            uint32_t o = 0;                            // first lane whose inclusive count exceeds g
-#pragma unroll
-            for (uint32_t st = 16; st > 0; st >>= 1) {
-                const uint32_t v = __shfl_sync(GB_FULL_MASK, incl, (o + st - 1) & 31);
-                if (v <= g) o += st;
-            }
-            o &= 31;
-            const uint32_t Uo = __shfl_sync(GB_FULL_MASK, U, o);
-            const uint32_t eo = __shfl_sync(GB_FULL_MASK, excl, o);
-            const uint32_t kn = 32u * (wg + o) + (lane < m ? select_bit(Uo, g - eo) : 0u);
-            // append entries 0..m-1 of kn at queue positions c..c+m-1
-            const uint32_t k_lo = __shfl_sync(GB_FULL_MASK, kn, (lane - c) & 31);
-            const uint32_t k_hi = __shfl_sync(GB_FULL_MASK, kn, (lane + 32u - c) & 31);
-            if (lane >= c && lane - c < m) kq = k_lo;
-            if (c + m >= 32u) {
-                tail_one(win, PR, KW, kq, true, n_lo, ks, i_start, prm, acc, ss, ctrl);
-                const uint32_t left = c + m - 32u;
-                if (lane < left) kq = k_hi;
-                c = left;
-            } else {
-                c += m;
-            }
-        }
-    }
-    if (c) tail_one(win, PR, KW, kq, lane < c, n_lo, ks, i_start, prm, acc, ss, ctrl);
-}
-
-// The same per-n phase with a lower-latency compaction: each step every lane
-// hands over the lowest open bit of its word, its slot in the warp's 64-entry
+// warp stored the open mask of each of its words (p_min above the
+// bit-parallel bound); here each step every lane hands over the lowest open
+// bit of its word, its slot in the warp's 64-entry
 // shared ring given by a ballot and a popcount (about three steps per group at
 // 10^12), and a full round of 32 is searched as soon as the ring holds one.
 struct OpenRing {
