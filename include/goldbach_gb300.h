@@ -205,6 +205,26 @@ int gb_verify_range_segments(uint64_t lo, uint64_t hi, gb_seg_record *buf, size_
                              size_t *n_written, gb_result *out);
 
 /*
+ * gb_verify_range_claimed -- cooperative form of gb_verify_range_segments:
+ * several callers (processes, on one or several GPUs) verify [lo, hi)
+ * together by claiming its tiles from *claim, a uint64_t in host memory that
+ * all of them can see (for example a shared-memory mapping), 0 before the
+ * first claim.  The kernels bump it with system-scope atomics: the paper's
+ * lock-free pool (Sec. 3.2) shared across devices.  Every caller must pass
+ * the same lo, hi and use the same seg_bits and tile_bits; the autotuner is
+ * not run.  This caller's records and result cover only the tiles it
+ * claimed (the other records are zero).  The callers' records merge record
+ * by record: counts, sums and histograms add, and the largest p_min with its
+ * smallest n wins.  That gives exactly the records of one
+ * gb_verify_range_segments call.  *claim is registered as mapped host
+ * memory for the duration of the call unless it already is.  A range that
+ * needs the bucket pre-pass (sqrt(n) at or above bucket_min) is refused with
+ * GB_EINVAL.  Otherwise returns as gb_verify_range_segments.
+ */
+int gb_verify_range_claimed(uint64_t lo, uint64_t hi, uint64_t *claim, gb_seg_record *buf, size_t cap,
+                            size_t *n_written, gb_result *out);
+
+/*
  * gb_verify_range_plain -- the plain per-segment form kept as the baseline
  * the persistent kernel is measured against: a host loop that, per segment,
  * launches a sieve kernel (bitset written to global memory), a search

@@ -104,6 +104,8 @@ def load(path: str = LIB_PATH):
         "gb_verify_range": ([U64, U64, P(GbResult)], ctypes.c_int),
         "gb_verify_range_segments": ([U64, U64, ctypes.c_void_p, sz, P(sz), P(GbResult)], ctypes.c_int),
         "gb_verify_range_plain": ([U64, U64, ctypes.c_void_p, sz, P(sz), P(GbResult)], ctypes.c_int),
+        "gb_verify_range_claimed": ([U64, U64, ctypes.c_void_p, ctypes.c_void_p, sz, P(sz), P(GbResult)],
+                                    ctypes.c_int),
         "gb_verify_range_async": ([U64, U64, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
         "gb_verify_range_noalloc": ([U64, U64, u32, u32, ctypes.c_void_p, ctypes.c_void_p],
                                     ctypes.c_int),
@@ -175,6 +177,20 @@ def gb_verify_range_segments(lo: int, hi: int, cap: int):
 
 def gb_verify_range_plain(lo: int, hi: int, cap: int = 0):
     return _segments("gb_verify_range_plain", lo, hi, cap)
+
+
+def gb_verify_range_claimed(lo: int, hi: int, claim_ptr: int, cap: int):
+    """Cooperative form: claim_ptr is the host address of a uint64 tile counter
+    shared by every caller (0 before the first claim).  Returns (records of
+    this caller's tiles, its aggregate, number of records)."""
+    lib = load()
+    buf = np.zeros(max(cap, 1), dtype=SEG_DTYPE)
+    n = ctypes.c_size_t(0)
+    r = GbResult()
+    rc = lib.gb_verify_range_claimed(lo, hi, ctypes.c_void_p(claim_ptr), buf.ctypes.data, cap,
+                                     ctypes.byref(n), ctypes.byref(r))
+    _check("gb_verify_range_claimed", rc, ok=(GB_OK, GB_COUNTEREXAMPLE))
+    return buf[:min(cap, n.value)], r.as_dict(), n.value
 
 
 def gb_verify_range_async(lo: int, hi: int, dev_out_ptr: int, stream_ptr: int = 0) -> None:

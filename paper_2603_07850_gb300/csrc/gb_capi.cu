@@ -1570,6 +1570,75 @@ int gb_verify_range_segments(uint64_t lo, uint64_t hi, gb_seg_record *buf, size_
     return g.h_result->status;
 }
 
+// Cooperative form: the tiles of [lo, hi) are claimed from *claim, a counter in
+// host memory that every cooperating caller (process, GPU) passes; this
+// caller's records and result cover only the tiles it claimed.
+int run_persistent_claimed(uint64_t lo, uint64_t hi, uint64_t *claim, CallPlan &cp)
+{
+    int rc = plan_range(lo, hi, cp);
+    if (rc) return rc;
+    if (!cp.n_total) return GB_OK;
+    if ((rc = prepare_common(cp))) return rc;
+    if (needs_buckets(cp)) {
+        set_error("gb_verify_range_claimed: the range needs the bucket pre-pass (sqrt(n) at or above "
+                  "bucket_min); split it with gb_verify_range instead");
+        return GB_EINVAL;
+    }
+    begin_progress(cp.ntiles);
+    const uint32_t tile_bits = (uint32_t)g.opt.tile_bits;
+    const int nt = (int)g.opt.threads;
+    const size_t smem = persistent_smem(tile_bits);
+    const void *fn = persistent_kernel_ptr((int)g.opt.wheel, nt, (int)g.opt.search_chunks);
+    int grid = 0;
+    if ((rc = ctx_grid(fn, nt, smem, &grid))) return rc;
+    bool registered = false;
+    cudaError_t e = cudaHostRegister(claim, sizeof *claim, cudaHostRegisterMapped | cudaHostRegisterPortable);
+    if (e == cudaSuccess) registered = true;
+    else if (e == cudaErrorHostMemoryAlreadyRegistered) cudaGetLastError();
+    else return cuda_status(e, "cudaHostRegister(claim counter)");
+    unsigned long long *d_claim = nullptr;
+    e = cudaHostGetDevicePointer((void **)&d_claim, claim, 0);
+    if (e == cudaSuccess) {
+        fill_params(cp, tile_bits, *g.h_params);
+        g.h_params->claim = d_claim;
+        e = cudaMemcpyAsync(g.d_params, g.h_params, sizeof(RangeParams), cudaMemcpyHostToDevice, g.stream);
+    }
+    Tables t = make_tables();
+    if (e == cudaSuccess) e = launch_clear(g.stream, g.d_params, g.d_recs, g.d_ctrl, 1, 4 * g.sms);
+    if (e == cudaSuccess)
+        e = launch_persistent((int)g.opt.wheel, nt, (int)g.opt.search_chunks, grid, smem, g.stream, g.d_params, t,
+                              g.d_recs, g.d_ctrl);
+    if (e == cudaSuccess)
+        e = launch_merge(g.stream, merge_grid_for(cp.nrec), g.d_params, g.d_recs, g.d_ctrl, g.d_parts, g.d_result);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g.h_result, g.d_result, sizeof(gb_result), cudaMemcpyDeviceToHost, g.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g.stream);
+    if (registered) cudaHostUnregister(claim);
+    if (e != cudaSuccess) return cuda_status(e, "claimed launch");
+    g.stats.kernel_launches += 3;
+    return GB_OK;
+}
+
+int gb_verify_range_claimed(uint64_t lo, uint64_t hi, uint64_t *claim, gb_seg_record *buf, size_t cap,
+                            size_t *n_written, gb_result *out)
+{
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    if (!g.inited) { set_error("gb_init has not been called"); return GB_EINVAL; }
+    if (!claim) { set_error("gb_verify_range_claimed: claim counter is NULL"); return GB_EINVAL; }
+    CallPlan cp;
+    int rc = run_persistent_claimed(lo, hi, claim, cp);
+    if (rc) { if (out) { empty_result(out); out->status = rc; } return rc; }
+    if (!cp.n_total) {
+        if (n_written) *n_written = 0;
+        empty_result(out);
+        return GB_OK;
+    }
+    if ((rc = copy_records(cp, buf, cap, n_written))) return rc;
+    if (out) *out = *g.h_result;
+    finish_stats(cp, *g.h_result);
+    return g.h_result->status;
+}
+
 int gb_verify_range_plain(uint64_t lo, uint64_t hi, gb_seg_record *buf, size_t cap,
                           size_t *n_written, gb_result *out)
 {

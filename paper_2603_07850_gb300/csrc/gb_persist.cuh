@@ -253,7 +253,8 @@ persistent_kernel(const RangeParams *__restrict__ prm_g, Tables t, DevRec *__res
     build_wheel_pattern<WHEEL, NT>(wpat);
     for (uint32_t i = threadIdx.x; i < KW; i += NT) PR[i] = t.PR[i];
     for (;;) {
-        if (threadIdx.x == 0) s.tile = prm.tile0 + atomicAdd(&ctrl->tile_ctr, 1ull);
+        if (threadIdx.x == 0)
+            s.tile = prm.tile0 + (prm.claim ? atomicAdd_system(prm.claim, 1ull) : atomicAdd(&ctrl->tile_ctr, 1ull));
         __syncthreads();
         const unsigned long long tile = s.tile;
         if (tile >= prm.tile_end) break;

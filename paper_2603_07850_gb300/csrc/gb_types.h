@@ -56,6 +56,8 @@ struct __align__(16) RangeParams {
     const unsigned long long *bk_off;  // bucket of tile t: entries [bk_off[t-tile0], bk_off[t-tile0+1])
     const uint32_t *bk_ent;            // window bit indices; nullptr = no buckets
     unsigned long long *progress;      // finished-tile counter in mapped host memory, or nullptr
+    unsigned long long *claim;         // tile counter shared by several callers (mapped host
+                                       // memory, system-scope atomics), or nullptr = Ctrl::tile_ctr
 };
 
 // Serving: one admitted request.  Its params have rec_bits = 40 so the whole

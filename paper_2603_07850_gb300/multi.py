@@ -3,8 +3,10 @@
 Ranks verify disjoint blocks of the range independently (no collective on
 the data path, the device form of the paper's pool needs none across GPUs);
 the only exchange is one gather of fixed-size results, merged in range
-order.  This module holds the host logic only; each rank's result comes
-from the library on its own GPU.
+order.  Alternatively the callers claim tiles of one range from a shared
+host counter (gb_verify_range_claimed) and merge their record arrays.  This
+module holds the host logic only; each caller's records come from the
+library on its own GPU.
 """
 from __future__ import annotations
 
@@ -53,6 +55,33 @@ def merge_results(parts: list[dict]) -> dict:
             out["counterexample_n"] = p["counterexample_n"]
         if p["status"] and not out["status"]:
             out["status"] = p["status"]
+    return out
+
+
+def merge_record_sets(sets):
+    """Merge the record arrays (SEG_DTYPE, same range and seg_bits) of callers
+    that each verified part of the tiles of one range, as from
+    gb_verify_range_claimed: counts, sums (mod 2^64) and histograms add, the
+    largest p_min wins with its smallest n, the smallest counterexample wins.
+    The result equals the records of one call over the whole range."""
+    import numpy as np
+    sets = [s for s in sets if len(s)]
+    if not sets:
+        return []
+    out = sets[0].copy()
+    for s in sets[1:]:
+        assert len(s) == len(out) and (s["n_first"] == out["n_first"]).all()
+        out["n_count"] += s["n_count"]
+        out["sum_pmin"] += s["sum_pmin"]                 # uint64 arithmetic wraps mod 2^64
+        out["wsum_pmin"] += s["wsum_pmin"]
+        out["hist"] += s["hist"]
+        out["n_slow"] += s["n_slow"]
+        better = (s["max_pmin"] > out["max_pmin"]) | (
+            (s["max_pmin"] == out["max_pmin"]) & (s["max_pmin"] > 0) & (s["argmax_n"] < out["argmax_n"]))
+        out["max_pmin"] = np.where(better, s["max_pmin"], out["max_pmin"])
+        out["argmax_n"] = np.where(better, s["argmax_n"], out["argmax_n"])
+        ce_a, ce_b = out["counterexample_n"], s["counterexample_n"]
+        out["counterexample_n"] = np.where((ce_a == 0) | ((ce_b != 0) & (ce_b < ce_a)), ce_b, ce_a)
     return out
 
 
