@@ -3,24 +3,27 @@
 // Sieve window (paper Sec. 3.1, rebuilt for sm_103a): the odd integers of a
 // window are one bit each, bit j <-> q = wbase + 2j, in shared memory.  A
 // window is built in three passes:
-//   1. fill    : every word is written once from a pre-sieved pattern of the
-//                wheel primes 3*5*7(*11*13) and in-register masks of the next
-//                few primes (no shared-memory read-modify-write at all);
+//   1. fill    : every word is written once as the AND of pre-sieved
+//                patterns (3*5*7*11*13, 17*19*23, 29*31; 3*5*7 with wheel 7)
+//                and, when configured, in-register masks of primes above 31
+//                (no shared-memory read-modify-write at all);
 //   2. marking : the remaining base primes p <= sqrt(q_hi) clear their odd
 //                multiples from p^2 on with shared-memory atomicAnd, one warp
-//                per prime for the dense small primes (tier A) and one lane
-//                per prime for the sparse large ones (tier B);
+//                per prime for the dense small primes (tier A, in an order
+//                balanced over the warps) and one lane per prime for the
+//                sparse large ones (tier B); primes above the bucket bound
+//                come from the pre-pass's buckets;
 //   3. fix-ups : q <= 1 cleared, the pattern primes themselves set again.
 // Overflow guards follow paper Sec. 3.4: a prime sieves only while
 // p*p <= q_hi (p < 2^32 so p*p cannot wrap), and the first multiple is found
 // from wbase mod p as a distance, never by forming a value above q_hi.
 //
-// p_min search (paper Sec. 3.1 phase 1, Sec. 5.3 bitwise direction): for the
-// 32 consecutive even n of one warp, candidate p = 2i+1 maps to the window
-// bit c - i with c the bit of q = n - 1.  Lane l of chunk t extracts the 32
-// window bits [c - 32t - 31, c - 32t] with one funnel shift of two words that
-// every lane of the warp shares (broadcast), ANDs them with the bit-reversed
-// candidate word t, and the smallest candidate is 32t + clz(mask).
+// Per-n p_min search (paper Sec. 3.1 phase 1), the search_chunks = 0 form and
+// the tail of the bit-parallel one (gb_search.cuh): for one n, candidate
+// p = 2i+1 maps to the window bit c - i with c the bit of q = n - 1.  Chunk t
+// is the 32 window bits [c - 32t - 31, c - 32t], one funnel shift of two
+// words, ANDed with the bit-reversed candidate word t; the smallest
+// candidate is 32t + clz(mask).
 //
 // Slow path (paper Sec. 3.3, moved onto the GPU): an n with no candidate
 // p <= P_max is finished by its warp, 32 odd candidates p > P_max per step,

@@ -6,14 +6,15 @@
 // by the constant 31 - (i mod 32) (paper Sec. 5.3: bitwise bulk marking,
 // 32 n per instruction).  A lane owns one word and walks the odd primes
 // p < 64 BC (BC <= 8, so p < 512) in ascending order (compile-time unrolled);
-// each candidate
-// resolves the bits that are still open:
+// each candidate resolves the bits that are still open:
 //     x  = funnelshift(window words);  nw = x & ~V;  V |= x;
-// and records p in bit-sliced form (plane j gets nw when bit j of p is 1).
-// The record statistics of the word then come from the planes with popcounts:
-// sum, wsum, the log2 histogram and the max with its smallest n.  The few n
-// left open (p_min >= 64 BC) are compacted across the warp and finish with
-// the per-n search from chunk BC on, then the exact slow path.
+// and records p in bit-sliced form (plane j gets nw when bit j of p is 1;
+// planes 5.. once per 32-wide range of candidates).  The record statistics of
+// the word then come from the planes with popcounts: sum, wsum, the log2
+// histogram and the max with its smallest n.  The few n left open
+// (p_min >= 64 BC) are compacted through a per-warp shared ring into full
+// rounds of 32 and finish with the per-n search from chunk BC on, then the
+// exact slow path.
 #pragma once
 #include "gb_device.cuh"
 
