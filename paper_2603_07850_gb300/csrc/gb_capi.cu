@@ -126,7 +126,7 @@ struct Ctx {
     uint64_t aperm_key[5] = {0, 0, 0, 0, 0};
     std::map<uint64_t, uint32_t> odd_primes_below;  // cache: bound -> #odd primes below it
     char dev_name[256] = {0};
-    struct TuneCfg { int64_t tile_bits, threads, search_chunks, pattern_max, search_pmax, tier_b_min; };
+    struct TuneCfg { int64_t tile_bits, threads, search_chunks, pattern_max, search_pmax, tier_b_min, wheel; };
     std::map<std::string, TuneCfg> tuned;       // autotuner results by range class
     bool ev_pending = false;
 };
@@ -259,7 +259,8 @@ uint32_t bitrev32(uint32_t x)
     return r;
 }
 
-Tables make_tables()
+// Tables of one launch; `wheel` is the WHEEL of the kernel that gets them.
+Tables make_tables(int wheel)
 {
     Tables t{};
     t.primes = g.d_primes;
@@ -272,14 +273,14 @@ Tables make_tables()
     // on), the rest by in-register masks
     static const uint32_t pat[14] = {11, 13, 17, 19, 23, 29, 31, 37, 41, 43, 47, 53, 59, 61};
     t.groups = 0;
-    if (g.opt.wheel == 13 && g.opt.pattern_max >= 23) t.groups = 1;
-    if (g.opt.wheel == 13 && g.opt.pattern_max >= 31) t.groups = 2;
-    t.pat_lo = g.opt.wheel == 13 ? 2u + (t.groups >= 1 ? 3u : 0u) + (t.groups >= 2 ? 2u : 0u) : 0u;
-    uint32_t hi = g.opt.wheel == 13 ? 2u : 0u;
+    if (wheel == 13 && g.opt.pattern_max >= 23) t.groups = 1;
+    if (wheel == 13 && g.opt.pattern_max >= 31) t.groups = 2;
+    t.pat_lo = wheel == 13 ? 2u + (t.groups >= 1 ? 3u : 0u) + (t.groups >= 2 ? 2u : 0u) : 0u;
+    uint32_t hi = wheel == 13 ? 2u : 0u;
     while (hi < 14 && pat[hi] <= (uint32_t)g.opt.pattern_max) hi++;
     t.pat_hi = std::max(hi, t.pat_lo);
-    uint32_t lim = (uint32_t)g.opt.wheel;
-    if (hi > (g.opt.wheel == 13 ? 2u : 0u)) lim = std::max(lim, pat[hi - 1]);
+    uint32_t lim = (uint32_t)wheel;
+    if (hi > (wheel == 13 ? 2u : 0u)) lim = std::max(lim, pat[hi - 1]);
     t.iA0 = (uint32_t)(std::upper_bound(g.h_small.begin(), g.h_small.end(), lim) - g.h_small.begin());
     t.iB0 = (uint32_t)(std::lower_bound(g.h_small.begin(), g.h_small.end(),
                                         (uint32_t)g.opt.tier_b_min) - g.h_small.begin());
@@ -293,16 +294,19 @@ Tables make_tables()
     return t;
 }
 
+Tables make_tables() { return make_tables((int)g.opt.wheel); }
+
 size_t window_words(uint32_t tile_bits)
 {
     return ((((size_t)1 << tile_bits) + 32ull * g.k_words) / 32 + 2 + 3) & ~(size_t)3;
 }
 
-size_t persistent_smem(uint32_t tile_bits)
+size_t persistent_smem(uint32_t tile_bits, int wheel)
 {
-    return 4ull * (wheel_pattern_words((int)g.opt.wheel) + ((g.k_words + 3) & ~3u) +
-                   window_words(tile_bits));
+    return 4ull * (wheel_pattern_words(wheel) + ((g.k_words + 3) & ~3u) + window_words(tile_bits));
 }
+
+size_t persistent_smem(uint32_t tile_bits) { return persistent_smem(tile_bits, (int)g.opt.wheel); }
 
 // Grow the device base-prime table to every prime <= need (or base_limit).
 int ensure_table(uint64_t need)
@@ -711,7 +715,7 @@ using TuneCfg = Ctx::TuneCfg;
 TuneCfg current_cfg()
 {
     return TuneCfg{g.opt.tile_bits, g.opt.threads, g.opt.search_chunks, g.opt.pattern_max,
-                   g.opt.search_pmax, g.opt.tier_b_min};
+                   g.opt.search_pmax, g.opt.tier_b_min, g.opt.wheel};
 }
 
 int apply_cfg(const TuneCfg &c)
@@ -723,6 +727,7 @@ int apply_cfg(const TuneCfg &c)
     g.opt.pattern_max = c.pattern_max;
     g.opt.search_pmax = c.search_pmax;
     g.opt.tier_b_min = c.tier_b_min;
+    g.opt.wheel = c.wheel;
     g.gkey = GraphKey{};
     return pr ? build_candidates() : GB_OK;
 }
@@ -772,9 +777,9 @@ void load_tune_file()
     FILE *f = fopen(path, "r");
     if (!f) return;
     char key[400];
-    long long a, b, c, d, e, h;
-    while (fscanf(f, "%399s %lld %lld %lld %lld %lld %lld", key, &a, &b, &c, &d, &e, &h) == 7)
-        g.tuned[key] = TuneCfg{a, b, c, d, e, h};
+    long long a, b, c, d, e, h, w;
+    while (fscanf(f, "%399s %lld %lld %lld %lld %lld %lld %lld", key, &a, &b, &c, &d, &e, &h, &w) == 8)
+        g.tuned[key] = TuneCfg{a, b, c, d, e, h, w};
     fclose(f);
 }
 
@@ -785,10 +790,10 @@ void save_tune_file()
     FILE *f = fopen(path, "w");
     if (!f) return;
     for (const auto &kv : g.tuned)
-        fprintf(f, "%s %lld %lld %lld %lld %lld %lld\n", kv.first.c_str(), (long long)kv.second.tile_bits,
+        fprintf(f, "%s %lld %lld %lld %lld %lld %lld %lld\n", kv.first.c_str(), (long long)kv.second.tile_bits,
                 (long long)kv.second.threads, (long long)kv.second.search_chunks,
                 (long long)kv.second.pattern_max, (long long)kv.second.search_pmax,
-                (long long)kv.second.tier_b_min);
+                (long long)kv.second.tier_b_min, (long long)kv.second.wheel);
     fclose(f);
 }
 
@@ -812,10 +817,11 @@ int maybe_autotune(CallPlan &cp)
         const std::vector<std::pair<int64_t TuneCfg::*, std::vector<int64_t>>> axes = {
             {&TuneCfg::search_chunks, {4, 6, 8}},
             {&TuneCfg::tier_b_min, {4096, 16384, 65536}},
-            {&TuneCfg::threads, {512, 1024}},
-            {&TuneCfg::tile_bits, {18, 19, 20}},
+            {&TuneCfg::threads, {256, 512, 1024}},              // 4, 2 or 1 CTAs per SM
+            {&TuneCfg::tile_bits, {15, 16, 17, 18, 19, 20, 21}}, // 2^21 never fits shared memory
+            {&TuneCfg::wheel, {7, 13}},
             {&TuneCfg::pattern_max, {13, 31, 61}},
-            {&TuneCfg::search_pmax, {0, 4096}},
+            {&TuneCfg::search_pmax, {0, 4096, 8192, 16384}},
         };
         for (int pass = 0; pass < 2; pass++) {
             for (const auto &ax : axes) {
@@ -1190,7 +1196,7 @@ struct ServeDev {
     Ctrl *d_ctrl = nullptr;
     unsigned int *h_flags = nullptr;
     const void *fn = nullptr;
-    int nt = 0, grid = 0;
+    int nt = 0, grid = 0, wheel = 13;           // the serving kernel's thread count and WHEEL
     size_t smem = 0;
     // bucket pre-pass of served requests: own stream, per-slot arrays from the
     // stream-ordered pool, released after the request's last batch
@@ -1238,8 +1244,9 @@ int ctx_serve_begin(int max_slots, int max_items)
     sv.nt = (int)g.opt.threads;
     int wheel = (int)g.opt.wheel, bc = (int)g.opt.search_chunks;
     sv.fn = serve_kernel_ptr(wheel, sv.nt, bc);
-    if (!sv.fn) { sv.nt = 1024; bc = 6; sv.fn = serve_kernel_ptr(13, 1024, 6); }
-    sv.smem = persistent_smem((uint32_t)g.opt.tile_bits);
+    if (!sv.fn) { sv.nt = 1024; bc = 6; wheel = 13; sv.fn = serve_kernel_ptr(13, 1024, 6); }
+    sv.wheel = wheel;                               // its tables and pattern block follow it
+    sv.smem = persistent_smem((uint32_t)g.opt.tile_bits, wheel);
     if ((rc = occupancy_grid(sv.fn, sv.nt, sv.smem, &sv.grid))) return rc;
     if (bc != 0) {                                   // the bit-parallel search needs slots
         sv.olist_wcap = olist_slice(sv.nt);
@@ -1344,7 +1351,7 @@ int ctx_serve_init_slot(int slot, const ServePlan &sp, uint64_t *bucket_bytes)
     }
     const uint32_t nt = (uint32_t)cp.ntiles;
     h.prm.bk_prime0 = count_odd_primes_below(B);
-    Tables t = make_tables();
+    Tables t = make_tables(sv.wheel);
     unsigned long long *off = nullptr;
     uint32_t *ent = nullptr;
     CK(cudaMemcpyAsync(&sv.d_slots[slot], &h, sizeof h, cudaMemcpyHostToDevice, sv.pp));
@@ -1387,7 +1394,7 @@ int ctx_serve_launch(int buf, size_t n)
 {
     CK(cudaMemcpyAsync(sv.d_items[buf], sv.h_items[buf], 8ull * n, cudaMemcpyHostToDevice, sv.st));
     CK(cudaMemsetAsync(sv.d_ctrl, 0, sizeof(Ctrl), sv.st));
-    Tables t = make_tables();
+    Tables t = make_tables(sv.wheel);
     t.olist = sv.d_olist;
     t.olist_wcap = sv.olist_wcap;
     t.olist_ctas = sv.d_olist ? (uint32_t)sv.grid : 0u;

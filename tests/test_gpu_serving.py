@@ -57,6 +57,23 @@ def test_results_same_alone_and_in_the_mix(gb):
     assert s["requests_completed"] >= len(reqs)
 
 
+@pytest.mark.parametrize("opts", [{"wheel": 7}, {"threads": 512, "search_chunks": 4}],
+                         ids=["wheel7", "threads512"])
+def test_settings_without_a_serving_build(gb, opts):
+    # these settings have no serving instantiation: the loop runs the
+    # wheel-13, 1,024-thread serving kernel with tables and shared memory
+    # sized for that kernel, and every result still equals the range call's
+    for k, v in opts.items():
+        gb.gb_set_option(k, v)
+    reqs = mix(12, W.SEED_C4 + 7, lo_max=10**12, w_hi_exp=7.0)
+    alone = [strip(gb.gb_verify_range(r.lo, r.hi)) for r in reqs]
+    tickets = [gb.gb_submit(r.lo, r.hi) for r in reqs]
+    for a, t in zip(alone, tickets):
+        st, res = gb.gb_poll(t, -1)
+        assert st == 0
+        assert a == strip(res)
+
+
 def test_small_requests_overtake_a_large_one(gb):
     ref_big = strip(gb.gb_verify_range(4, 4 * 10**10))      # also grows the table
     gb.gb_verify_range(10**12, 10**12 + 10)
