@@ -160,8 +160,11 @@ int gb_init(uint32_t p_max, uint32_t seg_bits);
  *   "autotune"      1 = before the first call of each range class (GPU, P_max,
  *                   log2 of the largest n), time the kernel configurations on a
  *                   probe at the top of the range and keep the fastest (tile_bits,
- *                   threads, search_chunks, pattern_max, search_pmax, tier_b_min); the choice
- *                   is cached, and saved to the file named by GB_TUNE_CACHE if set.
+ *                   threads, search_chunks, pattern_max, search_pmax, tier_b_min,
+ *                   wheel; combinations with no kernel build, or whose window
+ *                   does not fit shared memory, are skipped); the choice is
+ *                   cached, and saved to the file named by GB_TUNE_CACHE if set
+ *                   (one line per range class: key and the seven values).
  *                   The tuning call synchronises.  Results never depend on it.
  *   "search_pmax"   bound of the in-window candidate search, 0 = P_max (default 0);
  *                   n with p_min above it take the slow path, but n_slow and
