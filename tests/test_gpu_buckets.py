@@ -87,6 +87,35 @@ def test_high_offset_full_windows(gb, cfg):
     assert max(int(r["max_pmin"]) for r in recs) == agg["max_pmin"]
 
 
+# The largest minimal Goldbach partition found below 4 x 10^18 (Oliveira e
+# Silva, Herzog and Pardi, Math. Comp. 83 (2014)): n = 3,325,581,707,333,960,528
+# needs p = 9,781, and no smaller even n needs as much.
+RECORD_N, RECORD_P = 3325581707333960528, 9781
+
+
+def test_published_pmin_record(gb):
+    # base primes to 1.8e9 (bucketed), the record found in the window with
+    # P_max = 2^16 and by the Miller-Rabin slow path with P_max = 4096; the
+    # records agree except for n_slow
+    lo, hi = RECORD_N - 2 * 2048, RECORD_N + 2 * 2048
+    out = {}
+    for p_max in (1 << 16, 4096):
+        recs, agg = run(gb, lo, hi, p_max, 12)
+        assert agg["status"] == 0 and agg["counterexample_n"] == 0
+        assert agg["max_pmin"] == RECORD_P and agg["argmax_n"] == RECORD_N
+        out[p_max] = (recs, agg)
+    (r_win, a_win), (r_slow, a_slow) = out[1 << 16], out[4096]
+    assert a_win["n_slow"] == 0 and a_slow["n_slow"] >= 1
+    def without_nslow(recs):
+        out = []
+        for r in recs:
+            d = recutil.to_dict(recutil.canon(r))
+            del d["n_slow"]
+            out.append(d)
+        return out
+    assert without_nslow(r_win) == without_nslow(r_slow)
+
+
 def test_top_of_u64_range(gb):
     # hi = 2^64 - 1 includes n = 2^64 - 2; nothing may wrap
     e = W.C3_EDGE

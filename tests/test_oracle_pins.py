@@ -232,6 +232,26 @@ def test_invariants_1e18():
     assert recs[0].max_pmin == max(pm)
 
 
+# The largest minimal Goldbach partition found below 4 x 10^18 (Oliveira e
+# Silva, Herzog and Pardi, Math. Comp. 83 (2014), the verification the paper
+# builds on): n = 3,325,581,707,333,960,528 needs p = 9,781, and no smaller
+# even n needs as much.
+RECORD_N, RECORD_P = 3325581707333960528, 9781
+
+
+def test_published_pmin_record(base32):
+    # the window sieve and candidate walk reach the record's p, and in a
+    # window around it that p is the max with the record n as smallest argmax
+    lo, hi = RECORD_N - 2 * 2048, RECORD_N + 2 * 2048
+    st, recs, pm, _ = oracle.pmin_range(lo, hi, seg_bits=12, want_pmin=True,
+                                        base=(base32, (1 << 32) - 1))
+    assert st == 0 and len(recs) == 1
+    assert int(pm[2048]) == RECORD_P
+    assert recs[0].max_pmin == RECORD_P and recs[0].argmax_n == RECORD_N
+    assert all(int(x) < RECORD_P for x in pm[:2048])
+    _check_invariants(RECORD_N, RECORD_P)
+
+
 def test_top_of_u64_range(base32):
     # The last even n below 2^64 is 2^64 - 2; hi = 2^64 - 1 must include it
     # without any wrap.
