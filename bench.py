@@ -5,14 +5,20 @@
 One step = one pass of the whole hot path (claim -> window sieve -> p_min
 search -> slow path -> records -> merge) over every even n in [4, 10^12].
 
-value : device throughput of the persistent graph-free launch sequence on a
-        torch stream, timed with CUDA events per step, L2 flushed between
-        steps (a 512 MB write), max over ranks.
+value : device throughput of gb_verify_range_async on a torch stream, each
+        step one replay of the captured CUDA graph (set-params -> clear ->
+        persistent kernel -> merge), timed with CUDA events per step, L2
+        flushed between steps (a 512 MB write), max over ranks.
 e2e   : the same metric through the blocking C-ABI call gb_verify_range with
         host buffers (params H2D and the gb_result D2H inside the timed
         region), wall clock.
-plain : the plain per-segment form (one launch triple per segment plus a
-        status round trip), timed over the same range once.
+plain : the plain per-segment form (one launch sequence per segment plus a
+        status round trip), per-n search and bit-parallel search, each at the
+        best segment size of a sweep over [4, 10^11]; then both at 10^12, their
+        record arrays compared with the persistent kernel's, record by record.
+extra : C1 [4, 10^10] and C3a [10^18, 10^18 + 10^10) throughput, and a
+        shortened C4 serving run (p50 / p99 at 70% of measured capacity, with
+        an oracle sample).
 
 Multi-GPU (torchrun): every rank verifies its own block of 10^12 integers
 [r 10^12 + 4, (r + 1) 10^12], no collective on the data path (weak scaling);
@@ -52,6 +58,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default configuration")
     ap.add_argument("--option", action="append", default=[], metavar="KEY=VALUE",
                     help="set a library option before the run (repeatable; e.g. search_chunks=6)")
+    ap.add_argument("--no-extra", action="store_true", help="skip the C1, C3a and C4 figures")
+    ap.add_argument("--serve-requests", type=int, default=2000)
     return ap.parse_args()
 
 
@@ -312,6 +320,114 @@ def run_reference(args):
 # our arm
 # ---------------------------------------------------------------------------
 
+def kernel_seconds(gb, lo, hi, res, stream):
+    """One timed gb_verify_range_async on `stream`: the persistent kernel's
+    CUDA-event duration (time_kernel must be on) and the result."""
+    gb.gb_verify_range_async(lo, hi, res.data_ptr(), stream.cuda_stream)
+    stream.synchronize()
+    out = gb.result_from_bytes(bytes(res.cpu().numpy()))
+    return gb.gb_get_option("last_kernel_us") * 1e-6, out
+
+
+def measure_plain(gb, lo, hi, ref, flush, torch, stream, res):
+    """The plain per-segment form with the per-n search (the paper's shape)
+    and with the bit-parallel search.  Each sweeps plain_seg_bits over
+    [lo, lo + 10^11] and runs the whole range at its best size; every record
+    of both runs must equal the persistent kernel's.  Then the persistent
+    kernel with the per-n search over the whole range, for the ratio at equal
+    search."""
+    sweep_hi = min(hi, lo + 10**11)
+    bc = gb.gb_get_option("search_chunks") or 6
+    nrec = (ref["n_count"] + (1 << SEG_BITS) - 1) >> SEG_BITS
+    prec, pagg, _ = gb.gb_verify_range_segments(lo, hi, nrec)
+    out = {}
+    for name, pbc in (("per_n", 0), ("bit_parallel", bc)):
+        gb.gb_set_option("plain_search_chunks", pbc)
+        sweep = []
+        for sb in (22, 24, 26, 28, 30):
+            gb.gb_set_option("plain_seg_bits", sb)
+            gb.gb_verify_range_plain(lo, lo + 10**8)                 # buffers for this size
+            flush.fill_(7)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            _, r, _ = gb.gb_verify_range_plain(lo, sweep_hi, 0)
+            sweep.append({"plain_seg_bits": sb, "value": r["n_count"] / (time.perf_counter() - t)})
+        best = max(sweep, key=lambda x: x["value"])
+        gb.gb_set_option("plain_seg_bits", best["plain_seg_bits"])
+        flush.fill_(5)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        recs, r, n = gb.gb_verify_range_plain(lo, hi, nrec)
+        dt = time.perf_counter() - t
+        # the two forms agree on every field of every record, not just the totals
+        assert n == nrec and len(recs) == nrec and (recs == prec).all(), name
+        assert {k: r[k] for k in pagg if k != "status"} == {k: pagg[k] for k in pagg if k != "status"}
+        out[name] = {"value": r["n_count"] / dt, "unit": "even_n/s", "seconds": dt,
+                     "plain_seg_bits": best["plain_seg_bits"], "search_chunks": pbc, "sweep": sweep,
+                     "records_compared": nrec, "records_equal": True}
+    gb.gb_set_option("plain_search_chunks", 0)
+    gb.gb_set_option("plain_seg_bits", 26)
+    # the persistent kernel with the per-n search (the tuned shape, or the
+    # single-role kernel where the tuned pipelined shape has no per-n build)
+    keep = {k: gb.gb_get_option(k) for k in ("search_chunks", "autotune", "builder_warps", "tile_bits")}
+    gb.gb_set_option("autotune", 0)
+    gb.gb_set_option("search_chunks", 0)
+    try:
+        kernel_seconds(gb, lo, lo + 10**8, res, stream)
+    except gb.GbError:
+        gb.gb_set_option("builder_warps", 0)
+        gb.gb_set_option("tile_bits", 20)
+    with torch.cuda.stream(stream):
+        flush.fill_(9)
+    ks, r = kernel_seconds(gb, lo, hi, res, stream)
+    assert r["sum_pmin"] == ref["sum_pmin"] and r["argmax_n"] == ref["argmax_n"]
+    out["persistent_per_n"] = {"value": r["n_count"] / ks, "unit": "even_n/s", "kernel_s": ks,
+                               "builder_warps": gb.gb_get_option("builder_warps"),
+                               "tile_bits": gb.gb_get_option("tile_bits")}
+    for k, v in keep.items():
+        gb.gb_set_option(k, v)
+    return out
+
+
+def measure_extra(gb, torch, args):
+    """C1 and C3a throughput, and a shortened C4 serving run, each on a fresh
+    context (rank 0 only)."""
+    from paper_2603_07850_gb300 import workloads as W
+    import serve_bench
+    extra = {}
+    stream = torch.cuda.Stream()
+    res = torch.zeros(gb.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    # C1: every even n in [4, 1e10], records of 2^15, autotuned, graph replays
+    c = W.C1
+    gb.gb_init(c.p_max, c.seg_bits)
+    gb.gb_set_option("time_kernel", 1)
+    gb.gb_set_option("autotune", 1)
+    kernel_seconds(gb, c.lo, c.hi, res, stream)                    # tunes
+    ts = [kernel_seconds(gb, c.lo, c.hi, res, stream) for _ in range(5)]
+    ks = min(t for t, _ in ts)
+    extra["C1"] = {"workload": "every even n in [4, 1e10], records of 2^15", "value": ts[0][1]["n_count"] / ks,
+                   "unit": "even_n/s", "kernel_s": ks, "tile_bits": gb.gb_get_option("tile_bits"),
+                   "builder_warps": gb.gb_get_option("builder_warps"),
+                   "search_chunks": gb.gb_get_option("search_chunks")}
+    # C3a: [1e18, 1e18 + 1e10), base primes to 2^30 - 1, bucket pre-pass; the
+    # whole blocking call after a warm-up call that builds the table
+    c = W.C3A
+    gb.gb_init(c.p_max, c.seg_bits)
+    gb.gb_verify_range(c.lo, c.hi)
+    walls = []
+    for _ in range(3):
+        t = time.perf_counter()
+        r = gb.gb_verify_range(c.lo, c.hi)
+        walls.append(time.perf_counter() - t)
+    extra["C3a"] = {"workload": "[1e18, 1e18 + 1e10)", "value": r["n_count"] / min(walls), "unit": "even_n/s",
+                    "call_s": min(walls), "max_pmin": r["max_pmin"], "status": r["status"]}
+    gb.gb_shutdown()
+    # C4: the seeded serving stream, shortened
+    extra["C4"] = serve_bench.measure(gb, requests=args.serve_requests, capacity_requests=args.serve_requests,
+                                      load=0.7, oracle_sample=0.05)
+    return extra
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -350,6 +466,7 @@ def run_ours(args):
             step()
     stream.synchronize()
 
+    replays0 = gb.gb_stats()["graph_replays"]
     sampler = ClockSampler(local)
     sampler.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -370,6 +487,8 @@ def run_ours(args):
     if dist:
         dist.barrier()
     clocks = sampler.stop()
+    replays = gb.gb_stats()["graph_replays"] - replays0
+    assert replays == args.steps, (replays, args.steps)     # every timed step was one graph replay
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = sum(step_ms) / len(step_ms)
     out = gb.result_from_bytes(bytes(res.cpu().numpy()))
@@ -388,15 +507,8 @@ def run_ours(args):
     e2e_s = sum(e2e_t) / len(e2e_t)
 
     plain = None
-    if not args.no_plain:
-        flush.fill_(5)
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        _, pr, _ = gb.gb_verify_range_plain(lo, hi, 0)
-        plain_s = time.perf_counter() - t
-        assert pr["sum_pmin"] == out["sum_pmin"] and pr["argmax_n"] == out["argmax_n"]
-        plain = {"value": pr["n_count"] / plain_s, "unit": "even_n/s", "seconds": plain_s,
-                 "seg_bits": gb.gb_get_option("plain_seg_bits")}
+    if not args.no_plain and rank == 0:
+        plain = measure_plain(gb, lo, hi, out, flush, torch, stream, res)
 
     # max over ranks of the step time and of the e2e time; the results of the
     # ranks' blocks merge into one (the only exchange)
@@ -438,7 +550,9 @@ def run_ours(args):
                    "pattern_max": gb.gb_get_option("pattern_max"),
                    "search_pmax": gb.gb_get_option("search_pmax"),
                    "tier_b_min": gb.gb_get_option("tier_b_min"),
-                   "l2": "flushed between steps (512 MB write)", "form": "persistent"},
+                   "builder_warps": gb.gb_get_option("builder_warps"),
+                   "l2": "flushed between steps (512 MB write)", "form": "persistent",
+                   "launch": "one captured CUDA graph replay per step"},
         "e2e": {"value": tot_n / e2e_s, "unit": "even_n/s", "h2d_bytes_per_step": 64,
                 "d2h_bytes_per_step": gb.RESULT_BYTES},
         "gpu_launches": 4 * args.steps,
@@ -460,7 +574,11 @@ def run_ours(args):
                                       "logic/shift, integer mad, popc, conflict-free shared atomicAnd; the "
                                       "integer fraction divides by logic + mad (two pipes)"},
         "plain": plain,
-        "speedup_vs_plain": (tot_n / (ms * 1e-3)) / plain["value"] if plain else None,
+        "speedup_vs_plain": (tot_n / (ms * 1e-3)) / plain["per_n"]["value"] if plain else None,
+        "speedup_same_search_per_n": (plain["persistent_per_n"]["value"] / plain["per_n"]["value"]
+                                      if plain else None),
+        "speedup_same_search_bit_parallel": ((out["n_count"] / (ms * 1e-3)) / plain["bit_parallel"]["value"]
+                                             if plain else None),
         "result": {k: merged[k] for k in ("n_count", "max_pmin", "argmax_n", "sum_pmin", "n_slow")},
     }
     try:
@@ -480,6 +598,8 @@ def run_ours(args):
                           f"core, {dt:.1f} s wall"}
         except Exception as e:  # noqa: BLE001
             line["cpu_baseline_all_cores"] = {"value": None, "sample": f"failed: {e}"}
+    if not args.no_extra:
+        line["configs_extra"] = measure_extra(gb, torch, args)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -139,9 +139,22 @@ typedef struct {
 int gb_init(uint32_t p_max, uint32_t seg_bits);
 
 /*
- * gb_set_option -- tune the context.  Keys (value range):
- *   "tile_bits"     log2 even n per sieve tile, 10..20 (default 20)
- *   "threads"       threads per CTA: 256, 512 or 1024 (default 1024)
+ * gb_set_option -- tune the context.  The paper tunes a run with command-line
+ * flags and compile-time constants (Sec. 3.5: --gpus, --start, --progress,
+ * --batch-size; the segment size SEG_SIZE and the candidate bound P_SMALL of
+ * the reproducibility checklist); here the equivalents are context options,
+ * set between calls.  Keys (value range):
+ *   "tile_bits"     log2 even n per sieve tile, 10..20 (default 20; at most 19
+ *                   with the pipelined kernel and P_max = 2^16, whose CTA
+ *                   holds two windows)
+ *   "threads"       threads per CTA: 256, 512 or 1024, or 768 with the
+ *                   pipelined kernel (default 1024)
+ *   "builder_warps" 0 = single-role persistent kernel (every warp builds the
+ *                   window, then every warp searches it); 8, 12 or 16 = the
+ *                   pipelined kernel, in which that many warps build the next
+ *                   tile's window while the other warps search the current
+ *                   one (instantiated: 8 of 1024 or 768 threads, 12 or 16 of
+ *                   1024; wheel 13 only) (default 0)
  *   "ctas_per_sm"   persistent CTAs per SM, 1..4 (default: as many as fit)
  *   "wheel"         largest wheel prime pre-sieved by pattern: 7 or 13 (default 13)
  *   "pattern_max"   largest prime cleared by in-register patterns, 13..61 (default 31)
@@ -161,10 +174,12 @@ int gb_init(uint32_t p_max, uint32_t seg_bits);
  *                   log2 of the largest n), time the kernel configurations on a
  *                   probe at the top of the range and keep the fastest (tile_bits,
  *                   threads, search_chunks, pattern_max, search_pmax, tier_b_min,
- *                   wheel; combinations with no kernel build, or whose window
- *                   does not fit shared memory, are skipped); the choice is
+ *                   wheel, builder_warps; combinations with no kernel build are
+ *                   skipped, and a pipelined one takes the largest tile that
+ *                   fits shared memory); the choice is
  *                   cached, and saved to the file named by GB_TUNE_CACHE if set
- *                   (one line per range class: key and the seven values).
+ *                   (one line per range class: key and the eight values, the
+ *                   last builder_warps).
  *                   The tuning call synchronises.  Results never depend on it.
  *   "search_pmax"   bound of the in-window candidate search, 0 = P_max (default 0);
  *                   n with p_min above it take the slow path, but n_slow and
@@ -182,7 +197,10 @@ int gb_set_option(const char *key, int64_t value);
  * after the work has completed).  GB_EINVAL for an unknown key. */
 int gb_get_option(const char *key, int64_t *value);
 
-/* gb_shutdown -- stop the serving thread and free every device allocation. */
+/* gb_shutdown -- stop the serving thread, let in-flight work finish and free
+ * every device allocation and stream (the clean release the paper's error
+ * handling provides for failed GPU workers, Sec. 3.4).  Safe to call when
+ * gb_init has not been called. */
 void gb_shutdown(void);
 
 /* ---- range verification ------------------------------------------------------ */
@@ -207,24 +225,35 @@ int gb_verify_range(uint64_t lo, uint64_t hi, gb_result *out);
 int gb_verify_range_segments(uint64_t lo, uint64_t hi, gb_seg_record *buf, size_t cap,
                              size_t *n_written, gb_result *out);
 
+/* Claim block shared by the callers of gb_verify_range_claimed: host memory
+ * that all of them can see (for example a shared-memory mapping), zeroed
+ * before the first call. */
+typedef struct {
+    uint64_t next_tile;        /* next tile to claim; the kernels bump it with system-scope atomics */
+    uint64_t fingerprint;      /* set by the first caller: which range and configuration the tiles
+                                * index; 0 until then */
+} gb_claim_t;
+
 /*
  * gb_verify_range_claimed -- cooperative form of gb_verify_range_segments:
  * several callers (processes, on one or several GPUs) verify [lo, hi)
- * together by claiming its tiles from *claim, a uint64_t in host memory that
- * all of them can see (for example a shared-memory mapping), 0 before the
- * first claim.  The kernels bump it with system-scope atomics: the paper's
- * lock-free pool (Sec. 3.2) shared across devices.  Every caller must pass
- * the same lo, hi and use the same seg_bits and tile_bits; the autotuner is
- * not run.  This caller's records and result cover only the tiles it
- * claimed (the other records are zero).  The callers' records merge record
- * by record: counts, sums and histograms add, and the largest p_min with its
- * smallest n wins.  That gives exactly the records of one
- * gb_verify_range_segments call.  *claim is registered as mapped host
- * memory for the duration of the call unless it already is.  A range that
- * needs the bucket pre-pass (sqrt(n) at or above bucket_min) is refused with
- * GB_EINVAL.  Otherwise returns as gb_verify_range_segments.
+ * together by claiming its tiles from claim->next_tile.  This is the paper's
+ * lock-free work pool (Sec. 3.2, Alg. 1: workers take the next segment with
+ * an atomic increment of a shared counter) shared across devices.  Every
+ * caller must pass the same lo, hi and use the same seg_bits, tile_bits and
+ * P_max: the first caller stamps claim->fingerprint with them (atomic
+ * compare-and-swap) and a caller whose values differ is refused with
+ * GB_EINVAL before it claims anything.  The autotuner is not run.  This
+ * caller's records and result cover only the tiles it claimed (the other
+ * records are zero).  The callers' records merge record by record: counts,
+ * sums and histograms add, and the largest p_min with its smallest n wins.
+ * That gives exactly the records of one gb_verify_range_segments call.
+ * *claim is registered as mapped host memory for the duration of the call
+ * unless it already is.  A range that needs the bucket pre-pass (sqrt(n) at
+ * or above bucket_min) is refused with GB_EINVAL.  Otherwise returns as
+ * gb_verify_range_segments.
  */
-int gb_verify_range_claimed(uint64_t lo, uint64_t hi, uint64_t *claim, gb_seg_record *buf, size_t cap,
+int gb_verify_range_claimed(uint64_t lo, uint64_t hi, gb_claim_t *claim, gb_seg_record *buf, size_t cap,
                             size_t *n_written, gb_result *out);
 
 /*
@@ -286,30 +315,60 @@ int gb_verify_range_noalloc(uint64_t lo, uint64_t hi, uint32_t p_max, uint32_t s
 
 /*
  * gb_submit -- enqueue a range request [lo, hi) and return a ticket at once.
- * A scheduler thread admits requests while the device-memory budget allows,
- * interleaves their tiles in the persistent pool and finishes each request
- * independently.  Returns GB_OK, GB_EINVAL or GB_ENOMEM (never admissible).
+ * The paper runs one range per invocation and lets independent jobs take
+ * disjoint ranges (Sec. 3.5, --start); a request here is such a range, and
+ * many of them share the GPU.  A scheduler thread admits requests while the
+ * device-memory budget allows (the paper's pre-launch VRAM check, Sec. 3.5,
+ * applied per request), interleaves their tiles in the persistent pool
+ * (Sec. 3.2's claim-the-next-segment pool, over the tiles of every admitted
+ * request) and finishes each request independently, with its own status.
+ * *ticket is caller-owned.  Returns GB_OK, GB_EINVAL (NULL ticket, gb_init
+ * not called) or GB_ENOMEM (the request alone exceeds the budget).
  */
 int gb_submit(uint64_t lo, uint64_t hi, uint64_t *ticket);
 
 /*
  * gb_poll -- wait up to timeout_ms (0 = do not wait, < 0 = wait forever) for
  * a ticket.  Returns GB_PENDING while unfinished; otherwise the request's
- * status, with *out filled and the ticket released.
+ * status (status codes as for gb_verify_range, paper Sec. 3.4), with *out
+ * (caller-owned, may be NULL) filled and the ticket released.  A request's
+ * status comes only from its own tiles.  GB_EINVAL for an unknown ticket.
  */
 int gb_poll(uint64_t ticket, gb_result *out, int32_t timeout_ms);
 
 /* ---- introspection --------------------------------------------------------- */
 
+/* Progress of one gb_verify_range* call (see gb_progress). */
+typedef struct {
+    uint64_t tiles_done;       /* tiles finished (segments for the plain form)  */
+    uint64_t tiles_total;      /* tiles of the call                             */
+    uint64_t n_done;           /* even n in the finished tiles                  */
+    uint64_t n_total;          /* even n of the call                            */
+    double   elapsed_s;        /* host time since the call started              */
+    double   n_per_s;          /* n_done / elapsed_s (0 before the first tile)  */
+    double   eta_s;            /* (n_total - n_done) / n_per_s, -1 before the first tile */
+} gb_progress_t;
+
 /*
  * gb_progress -- progress of the gb_verify_range* call that is running (or
- * finished last): tiles done and tiles in total (segments for the plain
- * form).  Callable from any thread while the call runs, without waiting for
- * it: the persistent kernel counts finished tiles into mapped host memory
- * (paper Sec. 3.2, the progress monitor).  Returns GB_OK or GB_EINVAL.
+ * finished last): tiles and even n done, the rate so far and the estimated
+ * time left.  This is the paper's progress monitor (Sec. 3.2: a host thread
+ * reports the rate and remaining time while the GPUs work; Sec. 3.5, the
+ * --progress option).  Callable from any thread while the call runs, without
+ * waiting for it: the kernels count finished tiles into mapped host memory.
+ * `out` is caller-owned.  Returns GB_OK, or GB_EINVAL if out is NULL or
+ * gb_init has not been called.
  */
-int gb_progress(uint64_t *tiles_done, uint64_t *tiles_total);
+int gb_progress(gb_progress_t *out);
 
+/*
+ * gb_stats -- counters since gb_init (gb_stats_t): calls, tiles, even n
+ * verified, slow-path n, kernel launches and graph replays, served
+ * requests, base-table size and device bytes held.  The throughput
+ * statistics the paper's progress monitor prints (Sec. 3.2) and the launch
+ * counts its profiling section reports (Sec. 4.3) come from these.  `out` is
+ * caller-owned.  Returns GB_OK, or GB_EINVAL if out is NULL.
+ */
 int gb_stats(gb_stats_t *out);
 
 /*
@@ -322,6 +381,13 @@ int gb_stats(gb_stats_t *out);
  * caller-owned.  Returns GB_OK, GB_EINVAL (out is NULL) or GB_ECUDA.
  */
 int gb_measure_peaks(gb_peaks_t *out);
+
+/*
+ * gb_last_error -- text of the last error any call reported (paper Sec. 3.4:
+ * a failure is reported with a description instead of ending the process).
+ * The string belongs to the library and stays valid on the calling thread
+ * until its next gb_last_error call.  Empty when no error has occurred.
+ */
 const char *gb_last_error(void);
 
 #ifdef __cplusplus

@@ -68,6 +68,14 @@ class GbStats(ctypes.Structure):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
 
 
+class GbProgress(ctypes.Structure):
+    _fields_ = [("tiles_done", U64), ("tiles_total", U64), ("n_done", U64), ("n_total", U64),
+                ("elapsed_s", ctypes.c_double), ("n_per_s", ctypes.c_double), ("eta_s", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class GbPeaks(ctypes.Structure):
     _fields_ = [("int_logic_ops", ctypes.c_double), ("int_mad_ops", ctypes.c_double),
                 ("popc_ops", ctypes.c_double), ("smem_atomic_ops", ctypes.c_double),
@@ -112,7 +120,7 @@ def load(path: str = LIB_PATH):
         "gb_submit": ([U64, U64, P(U64)], ctypes.c_int),
         "gb_poll": ([U64, P(GbResult), i32], ctypes.c_int),
         "gb_stats": ([P(GbStats)], ctypes.c_int),
-        "gb_progress": ([P(U64), P(U64)], ctypes.c_int),
+        "gb_progress": ([P(GbProgress)], ctypes.c_int),
         "gb_measure_peaks": ([P(GbPeaks)], ctypes.c_int),
         "gb_last_error": ([], ctypes.c_char_p),
     }
@@ -153,36 +161,46 @@ def gb_shutdown() -> None:
     load().gb_shutdown()
 
 
-def gb_verify_range(lo: int, hi: int) -> dict:
+def gb_verify_range(lo: int, hi: int, check: bool = True) -> dict:
+    """check=False returns the result (its "status" field set) instead of
+    raising on an error status."""
     r = GbResult()
     rc = load().gb_verify_range(lo, hi, ctypes.byref(r))
-    _check("gb_verify_range", rc, ok=(GB_OK, GB_COUNTEREXAMPLE))
+    if check:
+        _check("gb_verify_range", rc, ok=(GB_OK, GB_COUNTEREXAMPLE))
     return r.as_dict()
 
 
-def _segments(fn_name: str, lo: int, hi: int, cap: int):
+def _segments(fn_name: str, lo: int, hi: int, cap: int, check: bool = True):
     lib = load()
     buf = np.zeros(max(cap, 1), dtype=SEG_DTYPE)
     n = ctypes.c_size_t(0)
     r = GbResult()
     rc = getattr(lib, fn_name)(lo, hi, buf.ctypes.data, cap, ctypes.byref(n), ctypes.byref(r))
-    _check(fn_name, rc, ok=(GB_OK, GB_COUNTEREXAMPLE))
+    if check:
+        _check(fn_name, rc, ok=(GB_OK, GB_COUNTEREXAMPLE))
     return buf[:min(cap, n.value)], r.as_dict(), n.value
 
 
-def gb_verify_range_segments(lo: int, hi: int, cap: int):
-    """Returns (records ndarray[SEG_DTYPE], aggregate dict, number of records)."""
-    return _segments("gb_verify_range_segments", lo, hi, cap)
+def gb_verify_range_segments(lo: int, hi: int, cap: int, check: bool = True):
+    """Returns (records ndarray[SEG_DTYPE], aggregate dict, number of records);
+    check=False returns them with the aggregate's "status" set instead of
+    raising on an error status."""
+    return _segments("gb_verify_range_segments", lo, hi, cap, check)
 
 
 def gb_verify_range_plain(lo: int, hi: int, cap: int = 0):
     return _segments("gb_verify_range_plain", lo, hi, cap)
 
 
+CLAIM_BYTES = 16              # sizeof(gb_claim_t): tile counter and fingerprint
+
+
 def gb_verify_range_claimed(lo: int, hi: int, claim_ptr: int, cap: int):
-    """Cooperative form: claim_ptr is the host address of a uint64 tile counter
-    shared by every caller (0 before the first claim).  Returns (records of
-    this caller's tiles, its aggregate, number of records)."""
+    """Cooperative form: claim_ptr is the host address of a gb_claim_t
+    (CLAIM_BYTES, zeroed before the first call) shared by every caller.
+    Returns (records of this caller's tiles, its aggregate, number of
+    records)."""
     lib = load()
     buf = np.zeros(max(cap, 1), dtype=SEG_DTYPE)
     n = ctypes.c_size_t(0)
@@ -215,21 +233,24 @@ def gb_submit(lo: int, hi: int) -> int:
     return t.value
 
 
-def gb_poll(ticket: int, timeout_ms: int = -1):
-    """Returns (status, result dict or None while pending)."""
+def gb_poll(ticket: int, timeout_ms: int = -1, check: bool = True):
+    """Returns (status, result dict or None while pending); check=False also
+    returns (status, result) for an error status instead of raising."""
     r = GbResult()
     rc = load().gb_poll(ticket, ctypes.byref(r), timeout_ms)
     if rc == GB_PENDING:
         return rc, None
-    _check("gb_poll", rc, ok=(GB_OK, GB_COUNTEREXAMPLE))
+    if check:
+        _check("gb_poll", rc, ok=(GB_OK, GB_COUNTEREXAMPLE))
     return rc, r.as_dict()
 
 
-def gb_progress():
-    """(tiles done, tiles total) of the running or last verification call."""
-    d, t = U64(0), U64(0)
-    _check("gb_progress", load().gb_progress(ctypes.byref(d), ctypes.byref(t)))
-    return d.value, t.value
+def gb_progress() -> dict:
+    """Progress of the running or last verification call: tiles_done,
+    tiles_total, n_done, n_total, elapsed_s, n_per_s, eta_s."""
+    p = GbProgress()
+    _check("gb_progress", load().gb_progress(ctypes.byref(p)))
+    return p.as_dict()
 
 
 def gb_stats() -> dict:

@@ -16,7 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgoldbach_gb300.so")
-SOURCES = ["gb_kernels.cu", "gb_persist_256.cu", "gb_persist_512.cu", "gb_persist_1024.cu",
+SOURCES = ["gb_kernels.cu", "gb_persist_256.cu", "gb_persist_512.cu", "gb_persist_1024.cu", "gb_pipe_8.cu",
+           "gb_pipe_16.cu",
            "gb_capi.cu", "gb_serve.cpp", "gb_noalloc.cu", "gb_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

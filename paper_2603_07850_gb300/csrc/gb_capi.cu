@@ -47,6 +47,7 @@ struct Options {
     int64_t mem_budget_mb = 8192;
     int64_t plain_seg_bits = 26;
     int64_t plain_slice_bits = 18;
+    int64_t plain_search_chunks = 0;   // plain form: 0 = per-n search kernel, 4/6/8 = bit-parallel
     int64_t use_graph = 1;
     int64_t slow_cap = 24;
     int64_t timeout_ms = 600000;
@@ -57,6 +58,7 @@ struct Options {
     int64_t search_pmax = 0;       // window search bound; 0 = P_max
     int64_t search_chunks = 4;     // bit-parallel search over p < 64 * this (0 = per-n search)
     int64_t autotune = 0;          // 1: tune the kernel configuration per range class
+    int64_t builder_warps = 0;     // > 0: pipelined kernel, this many warps build windows
 };
 
 struct GraphKey {
@@ -101,6 +103,13 @@ struct Ctx {
     // graph
     cudaGraphExec_t gexec = nullptr;
     GraphKey gkey;
+    // graph of gb_verify_range_async: set-params -> clear -> kernel -> merge
+    // into the caller's result; each call rewrites the set-params node's
+    // arguments in the instantiated graph and replays it on the caller's stream
+    cudaGraphExec_t aexec = nullptr;
+    cudaGraphNode_t anode = nullptr;
+    GraphKey akey;
+    const void *aout = nullptr;
     // plain-form buffers
     uint32_t *d_gwin = nullptr;
     size_t gwin_words = 0;
@@ -126,14 +135,28 @@ struct Ctx {
     uint64_t aperm_key[5] = {0, 0, 0, 0, 0};
     std::map<uint64_t, uint32_t> odd_primes_below;  // cache: bound -> #odd primes below it
     char dev_name[256] = {0};
-    struct TuneCfg { int64_t tile_bits, threads, search_chunks, pattern_max, search_pmax, tier_b_min, wheel; };
+    struct TuneCfg {
+        int64_t tile_bits, threads, search_chunks, pattern_max, search_pmax, tier_b_min, wheel, builder_warps;
+    };
     std::map<std::string, TuneCfg> tuned;       // autotuner results by range class
     bool ev_pending = false;
 };
 
 Ctx g;
+
+// The captured graphs bake in table, record and scratch pointers and launch
+// shapes: any change of those makes the next call capture again.
+void invalidate_graphs()
+{
+    g.gkey = GraphKey{};
+    g.akey = GraphKey{};
+}
+
 std::atomic<bool> g_ready{false};        // gb_init done: readable without the context lock
 std::atomic<unsigned long long> g_progress_total{0};   // tiles of the running call
+std::atomic<unsigned long long> g_progress_ntotal{0};  // its even n
+std::atomic<unsigned long long> g_progress_tile_n{0};  // even n per tile
+std::atomic<long long> g_progress_t0{0};               // its start, steady-clock ns
 std::atomic<unsigned long long *> g_progress_ptr{nullptr};
 uint32_t search_pmax();
 int build_candidates();
@@ -308,6 +331,30 @@ size_t persistent_smem(uint32_t tile_bits, int wheel)
 
 size_t persistent_smem(uint32_t tile_bits) { return persistent_smem(tile_bits, (int)g.opt.wheel); }
 
+// The range kernel of the current options: the pipelined kernel when
+// builder_warps > 0 (its CTA holds two windows), else the persistent one.
+const void *range_kernel()
+{
+    if (g.opt.builder_warps > 0)
+        return pipe_kernel_ptr((int)g.opt.wheel, (int)g.opt.builder_warps, (int)g.opt.threads,
+                               (int)g.opt.search_chunks);
+    return persistent_kernel_ptr((int)g.opt.wheel, (int)g.opt.threads, (int)g.opt.search_chunks);
+}
+
+size_t range_smem(uint32_t tile_bits)
+{
+    if (g.opt.builder_warps <= 0) return persistent_smem(tile_bits);
+    return 4ull * (wheel_pattern_words((int)g.opt.wheel) + ((g.k_words + 3) & ~3u) +
+                   2ull * pipe_window_words(tile_bits, g.k_words));
+}
+
+// Threads that build windows and threads that search them, per CTA.
+int builder_threads() { return g.opt.builder_warps > 0 ? 32 * (int)g.opt.builder_warps : (int)g.opt.threads; }
+int searcher_threads()
+{
+    return g.opt.builder_warps > 0 ? (int)g.opt.threads - 32 * (int)g.opt.builder_warps : (int)g.opt.threads;
+}
+
 // Grow the device base-prime table to every prime <= need (or base_limit).
 int ensure_table(uint64_t need)
 {
@@ -345,25 +392,28 @@ int ensure_table(uint64_t need)
         if (e == cudaSuccess) e = cudaStreamSynchronize(g.stream);
         uint32_t *np = nullptr;
         unsigned long long *nr = nullptr;
-        if (e == cudaSuccess && (rc = dev_alloc(&np, 4ull * total)) == GB_OK &&
-            (rc = dev_alloc(&nr, 8ull * total)) == GB_OK) {
-            e = launch_table_compact(g.stream, bits, gwords, bc, bo, L, np, nr, 0);
+        const uint64_t padded = (total + 3) & ~3ull;       // four-wide loads read up to here
+        if (e == cudaSuccess && (rc = dev_alloc(&np, 4ull * padded)) == GB_OK &&
+            (rc = dev_alloc(&nr, 8ull * padded)) == GB_OK) {
+            e = cudaMemsetAsync(np + total, 0, 4ull * (padded - total), g.stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(nr + total, 0, 8ull * (padded - total), g.stream);
+            if (e == cudaSuccess) e = launch_table_compact(g.stream, bits, gwords, bc, bo, L, np, nr, 0);
             if (e == cudaSuccess) e = cudaStreamSynchronize(g.stream);
             if (e == cudaSuccess) e = cudaDeviceSynchronize();   // no launch may still read the old table
             if (e == cudaSuccess) {
-                dev_free(&g.d_primes, 4ull * g.nprimes);
-                dev_free(&g.d_recip, 8ull * g.nprimes);
+                dev_free(&g.d_primes, 4ull * ((g.nprimes + 3) & ~3ull));
+                dev_free(&g.d_recip, 8ull * ((g.nprimes + 3) & ~3ull));
                 g.d_primes = np;
                 g.d_recip = nr;
                 g.nprimes = total;
                 g.table_limit = L;
                 np = nullptr;
                 nr = nullptr;
-                g.gkey = GraphKey{};                 // tables changed: recapture
+                invalidate_graphs();                 // tables changed: recapture
             }
         }
-        dev_free(&np, 4ull * total);
-        dev_free(&nr, 8ull * total);
+        dev_free(&np, 4ull * padded);
+        dev_free(&nr, 8ull * padded);
     }
     dev_free(&bc, 4ull * nb);
     dev_free(&bo, 8ull * (nb + 1));
@@ -381,7 +431,7 @@ int ensure_records(uint64_t nrec)
     int rc = dev_alloc(&g.d_recs, sizeof(DevRec) * cap);
     if (rc) return rc;
     g.rec_cap = cap;
-    g.gkey = GraphKey{};
+    invalidate_graphs();
     return GB_OK;
 }
 
@@ -436,10 +486,20 @@ void empty_result(gb_result *out)
     out->status = GB_OK;
 }
 
-void begin_progress(uint64_t tiles)
+long long steady_ns()
+{
+    return (long long)std::chrono::duration_cast<std::chrono::nanoseconds>(
+               std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// A call of `tiles` tiles of tile_n even n each (n_total in all) starts.
+void begin_progress(uint64_t tiles, uint64_t n_total, uint64_t tile_n)
 {
     if (g.h_progress) *(volatile unsigned long long *)g.h_progress = 0;
     g_progress_total = tiles;
+    g_progress_ntotal = n_total;
+    g_progress_tile_n = tile_n;
+    g_progress_t0 = steady_ns();
 }
 
 int prepare_common(const CallPlan &cp)
@@ -471,18 +531,20 @@ int occupancy_grid(const void *fn, int nt, size_t smem, int *grid)
 
 // Open-mask slots per warp for the bit-parallel search: one u32 per word of
 // the warp's share of a tile, i.e. 32 x (its groups of 32 words).
-uint32_t olist_slice(int nt)
+uint32_t olist_slice(int nt, uint32_t tile_bits)
 {
     const uint64_t nwarp = (uint64_t)nt / 32;
-    const uint64_t groups = ((1ull << g.opt.tile_bits) + 1024 * nwarp - 1) / (1024 * nwarp);
+    const uint64_t groups = ((1ull << tile_bits) + 1024 * nwarp - 1) / (1024 * nwarp);
     return (uint32_t)(32 * groups);
 }
 
+uint32_t olist_slice(int nt) { return olist_slice(nt, (uint32_t)g.opt.tile_bits); }
+
 // The context's open-mask slots for a persistent launch of `grid` CTAs.
-int ensure_olist(int grid, int nt)
+int ensure_olist(int grid, int nt, uint32_t tile_bits, bool bulk)
 {
-    if (g.opt.search_chunks == 0) { g.olist_wcap = 0; g.olist_ctas = 0; return GB_OK; }
-    const uint32_t wcap = olist_slice(nt);
+    if (!bulk) { g.olist_wcap = 0; g.olist_ctas = 0; return GB_OK; }
+    const uint32_t wcap = olist_slice(nt, tile_bits);
     const size_t need = (size_t)grid * (size_t)(nt / 32) * wcap;
     if (need > g.olist_cap) {
         dev_free(&g.d_olist, 4 * g.olist_cap);
@@ -544,8 +606,8 @@ int ensure_aperm(int nt)
 int ctx_grid(const void *fn, int nt, size_t smem, int *grid)
 {
     int rc = occupancy_grid(fn, nt, smem, grid);
-    if (!rc) rc = ensure_aperm(nt);
-    return rc ? rc : ensure_olist(*grid, nt);
+    if (!rc) rc = ensure_aperm(builder_threads());
+    return rc ? rc : ensure_olist(*grid, searcher_threads(), (uint32_t)g.opt.tile_bits, g.opt.search_chunks != 0);
 }
 
 int merge_grid_for(uint64_t nrec)
@@ -566,8 +628,7 @@ int enqueue_persistent(cudaStream_t st, const CallPlan &cp, gb_result *dev_out, 
         if (!g.ev1) CK(cudaEventCreate(&g.ev1));
         CK(cudaEventRecord(g.ev0, st));
     }
-    CK(launch_persistent((int)g.opt.wheel, (int)g.opt.threads, (int)g.opt.search_chunks, grid, smem, st, g.d_params, t, g.d_recs,
-                         g.d_ctrl));
+    CK(launch_range_kernel(range_kernel(), (int)g.opt.threads, grid, smem, st, g.d_params, t, g.d_recs, g.d_ctrl));
     if (timed) {
         CK(cudaEventRecord(g.ev1, st));
         g.ev_pending = true;
@@ -685,8 +746,7 @@ int run_persistent_buckets(const CallPlan &cp, int grid, size_t smem, int mg, gb
         p.bk_ent = g.d_bk_ent;
         CK(launch_set_params(st, g.d_params, p));
         CK(cudaMemsetAsync(&g.d_ctrl->tile_ctr, 0, 8, st));
-        CK(launch_persistent((int)g.opt.wheel, (int)g.opt.threads, (int)g.opt.search_chunks, grid, smem, st, g.d_params, t, g.d_recs,
-                             g.d_ctrl));
+        CK(launch_range_kernel(range_kernel(), (int)g.opt.threads, grid, smem, st, g.d_params, t, g.d_recs, g.d_ctrl));
         launches += 5;
     }
     p.tile0 = 0;
@@ -715,7 +775,7 @@ using TuneCfg = Ctx::TuneCfg;
 TuneCfg current_cfg()
 {
     return TuneCfg{g.opt.tile_bits, g.opt.threads, g.opt.search_chunks, g.opt.pattern_max,
-                   g.opt.search_pmax, g.opt.tier_b_min, g.opt.wheel};
+                   g.opt.search_pmax, g.opt.tier_b_min, g.opt.wheel, g.opt.builder_warps};
 }
 
 int apply_cfg(const TuneCfg &c)
@@ -728,7 +788,8 @@ int apply_cfg(const TuneCfg &c)
     g.opt.search_pmax = c.search_pmax;
     g.opt.tier_b_min = c.tier_b_min;
     g.opt.wheel = c.wheel;
-    g.gkey = GraphKey{};
+    g.opt.builder_warps = c.builder_warps;
+    invalidate_graphs();
     return pr ? build_candidates() : GB_OK;
 }
 
@@ -750,8 +811,8 @@ float time_probe(const CallPlan &probe_in)
     CallPlan probe = probe_in;
     probe.ntiles = ((probe.n_total - 1) >> g.opt.tile_bits) + 1;
     const int nt = (int)g.opt.threads;
-    const size_t smem = persistent_smem((uint32_t)g.opt.tile_bits);
-    const void *fn = persistent_kernel_ptr((int)g.opt.wheel, nt, (int)g.opt.search_chunks);
+    const size_t smem = range_smem((uint32_t)g.opt.tile_bits);
+    const void *fn = range_kernel();
     if (!fn || smem > g.smem_optin) return -1.f;
     int grid = 0;
     if (ctx_grid(fn, nt, smem, &grid)) { cudaGetLastError(); return -1.f; }
@@ -777,9 +838,9 @@ void load_tune_file()
     FILE *f = fopen(path, "r");
     if (!f) return;
     char key[400];
-    long long a, b, c, d, e, h, w;
-    while (fscanf(f, "%399s %lld %lld %lld %lld %lld %lld %lld", key, &a, &b, &c, &d, &e, &h, &w) == 8)
-        g.tuned[key] = TuneCfg{a, b, c, d, e, h, w};
+    long long a, b, c, d, e, h, w, bw;
+    while (fscanf(f, "%399s %lld %lld %lld %lld %lld %lld %lld %lld", key, &a, &b, &c, &d, &e, &h, &w, &bw) == 9)
+        g.tuned[key] = TuneCfg{a, b, c, d, e, h, w, bw};
     fclose(f);
 }
 
@@ -790,10 +851,10 @@ void save_tune_file()
     FILE *f = fopen(path, "w");
     if (!f) return;
     for (const auto &kv : g.tuned)
-        fprintf(f, "%s %lld %lld %lld %lld %lld %lld %lld\n", kv.first.c_str(), (long long)kv.second.tile_bits,
+        fprintf(f, "%s %lld %lld %lld %lld %lld %lld %lld %lld\n", kv.first.c_str(), (long long)kv.second.tile_bits,
                 (long long)kv.second.threads, (long long)kv.second.search_chunks,
                 (long long)kv.second.pattern_max, (long long)kv.second.search_pmax,
-                (long long)kv.second.tier_b_min, (long long)kv.second.wheel);
+                (long long)kv.second.tier_b_min, (long long)kv.second.wheel, (long long)kv.second.builder_warps);
     fclose(f);
 }
 
@@ -815,6 +876,7 @@ int maybe_autotune(CallPlan &cp)
         TuneCfg best = current_cfg();
         float best_ms = time_probe(probe);
         const std::vector<std::pair<int64_t TuneCfg::*, std::vector<int64_t>>> axes = {
+            {&TuneCfg::builder_warps, {0, 8, 12, 16}},       // single-role or pipelined kernel
             {&TuneCfg::search_chunks, {4, 6, 8}},
             {&TuneCfg::tier_b_min, {4096, 16384, 65536}},
             {&TuneCfg::threads, {256, 512, 1024}},              // 4, 2 or 1 CTAs per SM
@@ -831,6 +893,11 @@ int maybe_autotune(CallPlan &cp)
                     if (c.*(ax.first) == best.*(ax.first)) continue;
                     if (c.search_pmax && c.search_pmax >= (int64_t)g.p_max) continue;
                     if ((rc = apply_cfg(c))) return rc;
+                    // the pipelined kernel holds two windows: take the largest
+                    // tile that fits next to the other values
+                    while (g.opt.tile_bits > 15 && range_smem((uint32_t)g.opt.tile_bits) > g.smem_optin)
+                        g.opt.tile_bits--;
+                    c.tile_bits = g.opt.tile_bits;
                     const float ms = time_probe(probe);
                     if (ms > 0.f && (best_ms < 0.f || ms < 0.99f * best_ms)) { best = c; best_ms = ms; }
                 }
@@ -846,6 +913,64 @@ int maybe_autotune(CallPlan &cp)
     return GB_OK;
 }
 
+// The async pipeline's graph for this configuration and result pointer,
+// captured on first use, with its set-params node given this call's params.
+int async_graph(const CallPlan &cp, const RangeParams &p, gb_result *dev_out, int grid, size_t smem, int mg)
+{
+    GraphKey key;
+    key.fn = range_kernel(); key.grid = grid; key.nt = (int)g.opt.threads; key.wheel = (int)g.opt.wheel;
+    key.merge_grid = mg; key.clear_records = g.opt.tile_bits < g.seg_bits ? 1 : 0; key.smem = smem;
+    key.recs = g.d_recs; key.olist = g.d_olist; key.olist_wcap = g.olist_wcap; key.olist_ctas = g.olist_ctas;
+    const Tables tk = make_tables();
+    key.aperm = tk.aperm; key.aperm_len = tk.aperm_len;
+    if (!g.aexec || !(key == g.akey) || g.aout != dev_out) {
+        if (g.aexec) { cudaGraphExecDestroy(g.aexec); g.aexec = nullptr; }
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(g.stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = launch_set_params(g.stream, g.d_params, p);
+        int rc = e == cudaSuccess ? enqueue_persistent(g.stream, cp, dev_out, grid, smem, mg)
+                                  : cuda_status(e, "params kernel");
+        cudaError_t e2 = cudaStreamEndCapture(g.stream, &graph);
+        if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
+        if (e2 != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_status(e2, "graph capture"); }
+        // the set-params node: the graph's kernel node that runs that kernel
+        size_t nn = 0;
+        e = cudaGraphGetNodes(graph, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (e == cudaSuccess && nn) e = cudaGraphGetNodes(graph, nodes.data(), &nn);
+        g.anode = nullptr;
+        for (size_t i = 0; e == cudaSuccess && i < nn && !g.anode; i++) {
+            cudaGraphNodeType ty;
+            if (cudaGraphNodeGetType(nodes[i], &ty) != cudaSuccess || ty != cudaGraphNodeTypeKernel) continue;
+            cudaKernelNodeParams kp;
+            if (cudaGraphKernelNodeGetParams(nodes[i], &kp) == cudaSuccess && kp.func == set_params_kernel_ptr())
+                g.anode = nodes[i];
+        }
+        if (e == cudaSuccess && !g.anode) e = cudaErrorInvalidValue;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&g.aexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            g.aexec = nullptr;
+            return cuda_status(e, "async graph");
+        }
+        g.akey = key;
+        g.aout = dev_out;
+        return GB_OK;                                  // captured with this call's params
+    }
+    RangeParams *dst = g.d_params;
+    RangeParams pv = p;
+    void *args[] = {(void *)&dst, (void *)&pv};
+    cudaKernelNodeParams kp{};
+    kp.func = (void *)set_params_kernel_ptr();
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(32);
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    CK(cudaGraphExecKernelNodeSetParams(g.aexec, g.anode, &kp));
+    return GB_OK;
+}
+
 int run_persistent(uint64_t lo, uint64_t hi, CallPlan &cp)
 {
     int rc = plan_range(lo, hi, cp);
@@ -853,11 +978,11 @@ int run_persistent(uint64_t lo, uint64_t hi, CallPlan &cp)
     if (!cp.n_total) return GB_OK;
     if ((rc = prepare_common(cp))) return rc;
     if ((rc = maybe_autotune(cp))) return rc;
-    begin_progress(cp.ntiles);
+    begin_progress(cp.ntiles, cp.n_total, 1ull << g.opt.tile_bits);
     const uint32_t tile_bits = (uint32_t)g.opt.tile_bits;
     const int nt = (int)g.opt.threads;
-    const size_t smem = persistent_smem(tile_bits);
-    const void *fn = persistent_kernel_ptr((int)g.opt.wheel, nt, (int)g.opt.search_chunks);
+    const size_t smem = range_smem(tile_bits);
+    const void *fn = range_kernel();
     int grid = 0;
     if ((rc = ctx_grid(fn, nt, smem, &grid))) return rc;
     const int mg = merge_grid_for(cp.nrec);
@@ -961,7 +1086,19 @@ int run_plain(uint64_t lo, uint64_t hi, CallPlan &cp)
         if ((rc = dev_alloc(&g.d_gwin, 4 * need_words))) return rc;
         g.gwin_words = need_words;
     }
-    if (g.pm_cap < S) {
+    // bit-parallel search: 1,024-thread CTAs over sub-tiles of 2^sub_bits n
+    const int pbc = (int)g.opt.plain_search_chunks;
+    const uint32_t sub_bits = std::min<uint32_t>(sbits, std::max<uint32_t>(12, std::min<uint32_t>(17, sbits - 9)));
+    int bgrid = 0;
+    size_t bsmem = 0;
+    if (pbc) {
+        bsmem = 4ull * ((g.k_words + 3) & ~3u);
+        const void *bfn = plain_bulk_ptr(pbc);
+        if (!bfn) { set_error("plain_search_chunks must be 0, 4, 6 or 8"); return GB_EINVAL; }
+        if ((rc = occupancy_grid(bfn, 1024, bsmem, &bgrid))) return rc;
+        if ((rc = ensure_olist(bgrid, 1024, sub_bits, true))) return rc;
+        invalidate_graphs();                         // the persistent graph's slots changed
+    } else if (g.pm_cap < S) {
         dev_free(&g.d_pm, 4 * g.pm_cap);
         g.pm_cap = 0;
         if ((rc = dev_alloc(&g.d_pm, 4 * S))) return rc;
@@ -976,7 +1113,7 @@ int run_plain(uint64_t lo, uint64_t hi, CallPlan &cp)
     CK(cudaMemcpyAsync(g.d_params, g.h_params, sizeof(RangeParams), cudaMemcpyHostToDevice, g.stream));
     CK(launch_clear(g.stream, g.d_params, g.d_recs, g.d_ctrl, 1, 4 * g.sms));
     const uint64_t nseg = ((cp.n_total - 1) >> sbits) + 1;
-    begin_progress(nseg);
+    begin_progress(nseg, cp.n_total, S);
     const uint32_t chunk = (uint32_t)std::min<uint64_t>(1ull << 14, 1ull << g.seg_bits);
     uint64_t launches = 1;
     for (uint64_t s = 0; s < nseg; s++) {
@@ -990,9 +1127,18 @@ int run_plain(uint64_t lo, uint64_t hi, CallPlan &cp)
         const int grid = (int)((j_end + Z - 1) / Z);
         CK(launch_slice_sieve((int)g.opt.wheel, nt, grid, smem, g.stream, half_abs, neg ? 1 : 0, j_end, Z,
                               t, g.d_gwin, (uint32_t)g.gwin_words));
-        CK(launch_plain_search(g.stream, 8 * g.sms, g.d_params, g.d_gwin, g.d_PR, n_lo, cnt, g.d_pm,
-                               g.d_ctrl));
-        CK(launch_plain_reduce(g.stream, g.d_params, g.d_pm, k0, n_lo, cnt, chunk, g.d_recs, g.d_ctrl));
+        if (pbc) {
+            RangeParams ps = *g.h_params;
+            ps.tile_bits = sub_bits;
+            const uint32_t nsub = (uint32_t)((cnt + (1ull << sub_bits) - 1) >> sub_bits);
+            CK(launch_plain_bulk(pbc, std::min<int>(bgrid, (int)nsub), bsmem, g.stream, ps, k0 >> sub_bits, nsub, t,
+                                 g.d_gwin, g.d_recs, g.d_ctrl));
+            launches -= 1;
+        } else {
+            CK(launch_plain_search(g.stream, 8 * g.sms, g.d_params, g.d_gwin, g.d_PR, n_lo, cnt, g.d_pm,
+                                   g.d_ctrl));
+            CK(launch_plain_reduce(g.stream, g.d_params, g.d_pm, k0, n_lo, cnt, chunk, g.d_recs, g.d_ctrl));
+        }
         // the per-segment status round trip of the paper's worker loop
         CK(cudaMemcpyAsync(g.h_flags, &g.d_ctrl->flags, 4, cudaMemcpyDeviceToHost, g.stream));
         CK(cudaStreamSynchronize(g.stream));
@@ -1015,9 +1161,10 @@ void release_all()
     serve_stop();
     ctx_serve_end();
     if (g.gexec) { cudaGraphExecDestroy(g.gexec); g.gexec = nullptr; }
-    g.gkey = GraphKey{};
-    dev_free(&g.d_primes, 4ull * g.nprimes);
-    dev_free(&g.d_recip, 8ull * g.nprimes);
+    invalidate_graphs();
+    if (g.aexec) { cudaGraphExecDestroy(g.aexec); g.aexec = nullptr; }
+    dev_free(&g.d_primes, 4ull * ((g.nprimes + 3) & ~3ull));
+    dev_free(&g.d_recip, 8ull * ((g.nprimes + 3) & ~3ull));
     dev_free(&g.d_PR, 4ull * g.k_words);
     dev_free(&g.d_params, sizeof(RangeParams));
     dev_free(&g.d_ctrl, sizeof(Ctrl));
@@ -1074,7 +1221,7 @@ int build_candidates()
     if ((rc = dev_alloc(&g.d_PR, 4ull * kw))) return rc;
     g.k_words = kw;
     CK(cudaMemcpy(g.d_PR, PR.data(), 4ull * kw, cudaMemcpyHostToDevice));
-    g.gkey = GraphKey{};
+    invalidate_graphs();
     return GB_OK;
 }
 
@@ -1099,12 +1246,16 @@ int init_locked(uint32_t p_max, uint32_t seg_bits)
     // bootstrap base primes <= 2^16
     g.h_small = host_odd_primes(1u << 16);
     g.nprimes = g.h_small.size();
-    std::vector<unsigned long long> rc_h(g.nprimes);
+    // padded with zeros to a multiple of four entries (four-wide loads)
+    const size_t padded = (g.nprimes + 3) & ~(size_t)3;
+    std::vector<uint32_t> pr_h(g.h_small);
+    pr_h.resize(padded, 0u);
+    std::vector<unsigned long long> rc_h(padded, 0ull);
     for (size_t i = 0; i < g.nprimes; i++) rc_h[i] = 0xFFFFFFFFFFFFFFFFull / g.h_small[i];
-    if ((rc = dev_alloc(&g.d_primes, 4ull * g.nprimes))) return rc;
-    if ((rc = dev_alloc(&g.d_recip, 8ull * g.nprimes))) return rc;
-    CK(cudaMemcpy(g.d_primes, g.h_small.data(), 4ull * g.nprimes, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(g.d_recip, rc_h.data(), 8ull * g.nprimes, cudaMemcpyHostToDevice));
+    if ((rc = dev_alloc(&g.d_primes, 4ull * padded))) return rc;
+    if ((rc = dev_alloc(&g.d_recip, 8ull * padded))) return rc;
+    CK(cudaMemcpy(g.d_primes, pr_h.data(), 4ull * padded, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(g.d_recip, rc_h.data(), 8ull * padded, cudaMemcpyHostToDevice));
     g.table_limit = 1u << 16;
     if ((rc = dev_alloc(&g.d_params, sizeof(RangeParams)))) return rc;
     if ((rc = dev_alloc(&g.d_ctrl, sizeof(Ctrl)))) return rc;
@@ -1142,6 +1293,7 @@ const OptDesc kOpts[] = {
     {"mem_budget_mb", &Options::mem_budget_mb, 16, 1 << 22},
     {"plain_seg_bits", &Options::plain_seg_bits, 20, 30},
     {"plain_slice_bits", &Options::plain_slice_bits, 12, 20},
+    {"plain_search_chunks", &Options::plain_search_chunks, 0, 8},
     {"use_graph", &Options::use_graph, 0, 1},
     {"slow_cap", &Options::slow_cap, 6, 24},
     {"timeout_ms", &Options::timeout_ms, 1, 1ll << 40},
@@ -1152,6 +1304,7 @@ const OptDesc kOpts[] = {
     {"search_pmax", &Options::search_pmax, 0, 1 << 20},
     {"search_chunks", &Options::search_chunks, 0, 8},
     {"autotune", &Options::autotune, 0, 1},
+    {"builder_warps", &Options::builder_warps, 0, 16},
 };
 
 }  // namespace
@@ -1194,7 +1347,6 @@ struct ServeDev {
     SlotDev *d_slots = nullptr, *h_slots = nullptr;
     unsigned long long *d_items[2] = {nullptr, nullptr}, *h_items[2] = {nullptr, nullptr};
     Ctrl *d_ctrl = nullptr;
-    unsigned int *h_flags = nullptr;
     const void *fn = nullptr;
     int nt = 0, grid = 0, wheel = 13;           // the serving kernel's thread count and WHEEL
     size_t smem = 0;
@@ -1235,7 +1387,6 @@ int ctx_serve_begin(int max_slots, int max_items)
     sv.bk_ent.assign(max_slots, nullptr);
     if ((rc = dev_alloc(&sv.d_ctrl, sizeof(Ctrl)))) return rc;
     CK(cudaMallocHost((void **)&sv.h_slots, sizeof(SlotDev) * max_slots));
-    CK(cudaMallocHost((void **)&sv.h_flags, 4));
     for (int b = 0; b < 2; b++) {
         if ((rc = dev_alloc(&sv.d_items[b], 8ull * max_items))) return rc;
         CK(cudaMallocHost((void **)&sv.h_items[b], 8ull * max_items));
@@ -1282,7 +1433,6 @@ void ctx_serve_end()
         if (sv.ev[b]) cudaEventDestroy(sv.ev[b]);
     }
     if (sv.h_slots) cudaFreeHost(sv.h_slots);
-    if (sv.h_flags) cudaFreeHost(sv.h_flags);
     if (sv.st) cudaStreamDestroy(sv.st);
     if (sv.cp) cudaStreamDestroy(sv.cp);
     sv = ServeDev{};
@@ -1364,7 +1514,7 @@ int ctx_serve_init_slot(int slot, const ServePlan &sp, uint64_t *bucket_bytes)
     const unsigned long long total = *sv.h_total;
     CK(cudaMallocAsync((void **)&ent, 4ull * total + 16, sv.pp));
     CK(launch_bucket_prepass(sv.pp, 4 * g.sms, &sv.d_slots[slot].prm, t, h.prm.bk_prime0, 0, nt, sv.d_cnt,
-                             off, sv.d_cur, ent, 1, total, sv.d_ctrl));
+                             off, sv.d_cur, ent, 1, total, &sv.d_slots[slot].ctl));
     h.prm.bk_off = off;
     h.prm.bk_ent = ent;
     CK(cudaMemcpyAsync(&sv.d_slots[slot].prm, &h.prm, sizeof h.prm, cudaMemcpyHostToDevice, sv.pp));
@@ -1405,9 +1555,10 @@ int ctx_serve_launch(int buf, size_t n)
     return GB_OK;
 }
 
-// Wait for batch buf and read its status flags.  Touches only the serving
-// streams and buffers, so the caller does not hold the context lock.
-int ctx_serve_wait(int buf, unsigned int *flags, int64_t timeout_ms)
+// Wait for batch buf; later copies on the harvest stream are ordered after
+// it.  Touches only the serving streams and buffers, so the caller does not
+// hold the context lock.
+int ctx_serve_wait(int buf, int64_t timeout_ms)
 {
     if (timeout_ms >= 0) {
         // bounded wait: poll the batch's event, give up after timeout_ms
@@ -1424,19 +1575,20 @@ int ctx_serve_wait(int buf, unsigned int *flags, int64_t timeout_ms)
         }
     }
     CK(cudaStreamWaitEvent(sv.cp, sv.ev[buf], 0));
-    CK(cudaMemcpyAsync(sv.h_flags, &sv.d_ctrl->flags, 4, cudaMemcpyDeviceToHost, sv.cp));
     CK(cudaStreamSynchronize(sv.cp));
-    *flags = *sv.h_flags;
     return GB_OK;
 }
 
 // Copy a finished request's record out (its last batch has completed);
 // called without the context lock.
-int ctx_serve_fetch(int slot, const ServePlan &sp, unsigned int flags, gb_result *out)
+int ctx_serve_fetch(int slot, const ServePlan &sp, gb_result *out)
 {
+    // the record and the request's own control block are adjacent in its slot
+    static_assert(offsetof(SlotDev, ctl) == offsetof(SlotDev, acc) + sizeof(DevRec), "slot layout");
     DevRec *h = &sv.h_slots[slot].acc;
-    CK(cudaMemcpyAsync(h, &sv.d_slots[slot].acc, sizeof(DevRec), cudaMemcpyDeviceToHost, sv.cp));
+    CK(cudaMemcpyAsync(h, &sv.d_slots[slot].acc, sizeof(DevRec) + sizeof(Ctrl), cudaMemcpyDeviceToHost, sv.cp));
     CK(cudaStreamSynchronize(sv.cp));
+    const unsigned int flags = sv.h_slots[slot].ctl.flags;
     memset(out, 0, sizeof *out);
     out->n_first = sp.n0;
     out->n_count = h->n_count;
@@ -1446,7 +1598,8 @@ int ctx_serve_fetch(int slot, const ServePlan &sp, unsigned int flags, gb_result
     out->wsum_pmin = h->wsum;
     for (int b = 0; b < HIST_BINS; b++) out->hist[b] = h->hist[b];
     out->n_slow = h->n_slow;
-    out->counterexample_n = h->ce_inv ? ~h->ce_inv : 0;
+    const unsigned long long ci = h->ce_inv > sv.h_slots[slot].ctl.ce_inv ? h->ce_inv : sv.h_slots[slot].ctl.ce_inv;
+    out->counterexample_n = ci ? ~ci : 0;
     int st = GB_OK;
     if (flags & F_INTERNAL) st = GB_EINTERNAL;
     else if (flags & F_SLOWCAP) st = GB_ESLOWPATH_LIMIT;
@@ -1487,15 +1640,20 @@ int gb_set_option(const char *key, int64_t value)
             set_error("option %s out of range [%lld, %lld]", key, (long long)o.lo, (long long)o.hi);
             return GB_EINVAL;
         }
-        if (!strcmp(key, "threads") && value != 256 && value != 512 && value != 1024) {
-            set_error("threads must be 256, 512 or 1024");
+        if (!strcmp(key, "threads") && value != 256 && value != 512 && value != 768 && value != 1024) {
+            set_error("threads must be 256, 512, 768 (pipelined kernel only) or 1024");
+            return GB_EINVAL;
+        }
+        if (!strcmp(key, "builder_warps") && value != 0 && value != 8 && value != 12 && value != 16) {
+            set_error("builder_warps must be 0 (single-role kernel), 8, 12 or 16");
             return GB_EINVAL;
         }
         if (!strcmp(key, "bucket_min") && value != 0 && value < 64) {
             set_error("bucket_min must be 0 (automatic) or at least 64");
             return GB_EINVAL;
         }
-        if (!strcmp(key, "search_chunks") && value != 0 && value != 4 && value != 6 && value != 8) {
+        if ((!strcmp(key, "search_chunks") || !strcmp(key, "plain_search_chunks")) && value != 0 && value != 4 &&
+            value != 6 && value != 8) {
             set_error("search_chunks must be 0 (per-n search), 4, 6 or 8");
             return GB_EINVAL;
         }
@@ -1508,7 +1666,7 @@ int gb_set_option(const char *key, int64_t value)
             return GB_EINVAL;
         }
         g.opt.*o.field = value;
-        g.gkey = GraphKey{};
+        invalidate_graphs();
         if (!strcmp(key, "base_limit") && g.inited && value > 0) return ensure_table((uint64_t)value);
         if (!strcmp(key, "search_pmax") && g.inited) return build_candidates();
         return GB_OK;
@@ -1577,25 +1735,51 @@ int gb_verify_range_segments(uint64_t lo, uint64_t hi, gb_seg_record *buf, size_
     return g.h_result->status;
 }
 
-// Cooperative form: the tiles of [lo, hi) are claimed from *claim, a counter in
-// host memory that every cooperating caller (process, GPU) passes; this
-// caller's records and result cover only the tiles it claimed.
-int run_persistent_claimed(uint64_t lo, uint64_t hi, uint64_t *claim, CallPlan &cp)
+// What the tile indices of a claim block mean: the range's even-n grid, the
+// tile and record sizes and P_max.  Callers that share a block must agree on
+// all of them, or tiles would cover different n and records would not merge.
+uint64_t claim_fingerprint(const CallPlan &cp)
+{
+    uint64_t h = 0x6a09e667f3bcc909ull;                // splitmix64-style mixing of the fields
+    const uint64_t v[5] = {cp.n0, cp.n_total, (uint64_t)g.opt.tile_bits, (uint64_t)g.seg_bits, (uint64_t)g.p_max};
+    for (uint64_t x : v) {
+        h += x + 0x9e3779b97f4a7c15ull;
+        h = (h ^ (h >> 30)) * 0xbf58476d1ce4e5b9ull;
+        h = (h ^ (h >> 27)) * 0x94d049bb133111ebull;
+        h ^= h >> 31;
+    }
+    return h ? h : 1;                                  // 0 marks a block no caller has used
+}
+
+// Cooperative form: the tiles of [lo, hi) are claimed from claim->next_tile, a
+// counter in host memory that every cooperating caller (process, GPU) passes;
+// this caller's records and result cover only the tiles it claimed.
+int run_persistent_claimed(uint64_t lo, uint64_t hi, gb_claim_t *claim, CallPlan &cp)
 {
     int rc = plan_range(lo, hi, cp);
     if (rc) return rc;
     if (!cp.n_total) return GB_OK;
+    // the first caller stamps the block; the others must match it
+    uint64_t expected = 0;
+    const uint64_t fp = claim_fingerprint(cp);
+    if (!__atomic_compare_exchange_n(&claim->fingerprint, &expected, fp, false, __ATOMIC_ACQ_REL,
+                                     __ATOMIC_ACQUIRE) &&
+        expected != fp) {
+        set_error("gb_verify_range_claimed: the claim block belongs to another range or configuration "
+                  "(range, tile_bits, seg_bits and P_max must match every other caller's)");
+        return GB_EINVAL;
+    }
     if ((rc = prepare_common(cp))) return rc;
     if (needs_buckets(cp)) {
         set_error("gb_verify_range_claimed: the range needs the bucket pre-pass (sqrt(n) at or above "
                   "bucket_min); split it with gb_verify_range instead");
         return GB_EINVAL;
     }
-    begin_progress(cp.ntiles);
+    begin_progress(cp.ntiles, cp.n_total, 1ull << g.opt.tile_bits);
     const uint32_t tile_bits = (uint32_t)g.opt.tile_bits;
     const int nt = (int)g.opt.threads;
-    const size_t smem = persistent_smem(tile_bits);
-    const void *fn = persistent_kernel_ptr((int)g.opt.wheel, nt, (int)g.opt.search_chunks);
+    const size_t smem = range_smem(tile_bits);
+    const void *fn = range_kernel();
     int grid = 0;
     if ((rc = ctx_grid(fn, nt, smem, &grid))) return rc;
     bool registered = false;
@@ -1604,7 +1788,7 @@ int run_persistent_claimed(uint64_t lo, uint64_t hi, uint64_t *claim, CallPlan &
     else if (e == cudaErrorHostMemoryAlreadyRegistered) cudaGetLastError();
     else return cuda_status(e, "cudaHostRegister(claim counter)");
     unsigned long long *d_claim = nullptr;
-    e = cudaHostGetDevicePointer((void **)&d_claim, claim, 0);
+    e = cudaHostGetDevicePointer((void **)&d_claim, &claim->next_tile, 0);
     if (e == cudaSuccess) {
         fill_params(cp, tile_bits, *g.h_params);
         g.h_params->claim = d_claim;
@@ -1613,8 +1797,7 @@ int run_persistent_claimed(uint64_t lo, uint64_t hi, uint64_t *claim, CallPlan &
     Tables t = make_tables();
     if (e == cudaSuccess) e = launch_clear(g.stream, g.d_params, g.d_recs, g.d_ctrl, 1, 4 * g.sms);
     if (e == cudaSuccess)
-        e = launch_persistent((int)g.opt.wheel, nt, (int)g.opt.search_chunks, grid, smem, g.stream, g.d_params, t,
-                              g.d_recs, g.d_ctrl);
+        e = launch_range_kernel(fn, nt, grid, smem, g.stream, g.d_params, t, g.d_recs, g.d_ctrl);
     if (e == cudaSuccess)
         e = launch_merge(g.stream, merge_grid_for(cp.nrec), g.d_params, g.d_recs, g.d_ctrl, g.d_parts, g.d_result);
     if (e == cudaSuccess)
@@ -1626,7 +1809,7 @@ int run_persistent_claimed(uint64_t lo, uint64_t hi, uint64_t *claim, CallPlan &
     return GB_OK;
 }
 
-int gb_verify_range_claimed(uint64_t lo, uint64_t hi, uint64_t *claim, gb_seg_record *buf, size_t cap,
+int gb_verify_range_claimed(uint64_t lo, uint64_t hi, gb_claim_t *claim, gb_seg_record *buf, size_t cap,
                             size_t *n_written, gb_result *out)
 {
     std::lock_guard<std::recursive_mutex> lk(g_mu);
@@ -1683,12 +1866,12 @@ int gb_verify_range_async(uint64_t lo, uint64_t hi, gb_result *dev_out, void *st
     }
     if ((rc = prepare_common(cp))) return rc;
     if ((rc = maybe_autotune(cp))) return rc;          // synchronises while it tunes
-    begin_progress(cp.ntiles);
+    begin_progress(cp.ntiles, cp.n_total, 1ull << g.opt.tile_bits);
     const uint32_t tile_bits = (uint32_t)g.opt.tile_bits;
     const int nt = (int)g.opt.threads;
-    const size_t smem = persistent_smem(tile_bits);
+    const size_t smem = range_smem(tile_bits);
     int grid = 0;
-    if ((rc = ctx_grid(persistent_kernel_ptr((int)g.opt.wheel, nt, (int)g.opt.search_chunks), nt, smem, &grid))) return rc;
+    if ((rc = ctx_grid(range_kernel(), nt, smem, &grid))) return rc;
     if (needs_buckets(cp)) {
         // the pre-pass sizes its buffers on the host, so this form synchronises
         rc = run_persistent_buckets(cp, grid, smem, merge_grid_for(cp.nrec), dev_out, st, false);
@@ -1699,11 +1882,30 @@ int gb_verify_range_async(uint64_t lo, uint64_t hi, gb_result *dev_out, void *st
     }
     RangeParams p;
     fill_params(cp, tile_bits, p);
-    // the params travel as a kernel argument so no host buffer outlives the call
-    CK(launch_set_params(st, g.d_params, p));
-    if ((rc = enqueue_persistent(st, cp, dev_out, grid, smem, merge_grid_for(cp.nrec),
-                                 g.opt.time_kernel != 0)))
-        return rc;
+    const int mg = merge_grid_for(cp.nrec);
+    const bool timed = g.opt.time_kernel != 0;
+    if (g.opt.use_graph) {
+        // the params travel as an argument of the graph's first kernel, so no
+        // host buffer outlives the call
+        if ((rc = async_graph(cp, p, dev_out, grid, smem, mg))) return rc;
+        // timing events around the replay on the caller's stream (an event
+        // recorded inside a graph cannot be timed): the kernel plus the clear
+        // and merge launches before and after it, a few microseconds
+        if (timed) {
+            if (!g.ev0) CK(cudaEventCreate(&g.ev0));
+            if (!g.ev1) CK(cudaEventCreate(&g.ev1));
+            CK(cudaEventRecord(g.ev0, st));
+        }
+        CK(cudaGraphLaunch(g.aexec, st));
+        if (timed) {
+            CK(cudaEventRecord(g.ev1, st));
+            g.ev_pending = true;
+        }
+        g.stats.graph_replays++;
+    } else {
+        CK(launch_set_params(st, g.d_params, p));
+        if ((rc = enqueue_persistent(st, cp, dev_out, grid, smem, mg, timed))) return rc;
+    }
     g.stats.kernel_launches += 4;
     g.stats.tiles += cp.ntiles;
     g.stats.calls++;
@@ -1711,13 +1913,22 @@ int gb_verify_range_async(uint64_t lo, uint64_t hi, gb_result *dev_out, void *st
     return GB_OK;
 }
 
-int gb_progress(uint64_t *tiles_done, uint64_t *tiles_total)
+int gb_progress(gb_progress_t *out)
 {
-    if (!tiles_done || !tiles_total) return GB_EINVAL;
+    if (!out) return GB_EINVAL;
     const unsigned long long *p = g_progress_ptr.load();
     if (!p) { set_error("gb_init has not been called"); return GB_EINVAL; }
-    *tiles_done = *(const volatile unsigned long long *)p;
-    *tiles_total = g_progress_total.load();
+    memset(out, 0, sizeof *out);
+    out->tiles_total = g_progress_total.load();
+    out->tiles_done = std::min<uint64_t>(*(const volatile unsigned long long *)p, out->tiles_total);
+    out->n_total = g_progress_ntotal.load();
+    // every tile but the last holds tile_n even n
+    const unsigned long long tn = g_progress_tile_n.load();
+    out->n_done = out->tiles_done == out->tiles_total ? out->n_total
+                                                      : std::min<uint64_t>(out->tiles_done * tn, out->n_total);
+    out->elapsed_s = 1e-9 * (double)(steady_ns() - g_progress_t0.load());
+    out->n_per_s = out->elapsed_s > 0.0 ? (double)out->n_done / out->elapsed_s : 0.0;
+    out->eta_s = out->n_per_s > 0.0 ? (double)(out->n_total - out->n_done) / out->n_per_s : -1.0;
     return GB_OK;
 }
 

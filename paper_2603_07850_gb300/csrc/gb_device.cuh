@@ -191,23 +191,30 @@ static __device__ bool is_prime_u64(unsigned long long x)
     return true;
 }
 
+// slow_pmin's result when it stopped without an answer: its candidate cap ran
+// out, or another warp's had already run out (the call has failed).  Distinct
+// from 0, which means no p <= n/2 works (a counterexample).
+constexpr unsigned long long SLOW_GAVE_UP = ~0ull;
+
 // Warp-cooperative exact search for p_min(n) over odd p >= p_start (all lanes
-// call with the same n).  Returns p_min, or 0 with a flag set: F_COUNTEREX if
-// no p <= n/2 works (the counterexample is recorded), F_SLOWCAP if the
-// candidate cap ran out first.
+// call with the same n).  Returns p_min; 0 with F_COUNTEREX set if no
+// p <= n/2 works (the counterexample is recorded in *ce_inv); SLOW_GAVE_UP
+// with F_SLOWCAP set if the candidate cap ran out first.  flags and ce_inv
+// belong to the call (or, when serving, to the request) the n is part of.
 // Kept out of line: it runs for a tiny share of n, and inlined its 64-bit
 // Montgomery state would weigh on the register allocation of the hot loops.
 static __device__ __noinline__ unsigned long long slow_pmin(unsigned long long n, unsigned long long p_start,
-                                        uint32_t cap_log2, Ctrl *ctrl)
+                                        uint32_t cap_log2, unsigned int *flags,
+                                        unsigned long long *ce_inv)
 {
     const int lane = threadIdx.x & 31;
     const unsigned long long half = n >> 1;
     const unsigned long long steps = cap_log2 >= 6 ? (1ull << (cap_log2 - 6)) : 1ull;
     // once any warp has exhausted its cap the call has failed: stop early
     // (lane 0 reads the flag and broadcasts it so the warp stays converged)
-    unsigned int fl = lane == 0 ? *(volatile unsigned int *)&ctrl->flags : 0u;
+    unsigned int fl = lane == 0 ? *(volatile unsigned int *)flags : 0u;
     fl = __shfl_sync(GB_FULL_MASK, fl, 0);
-    if (fl & (F_SLOWCAP | F_INTERNAL)) return 0;
+    if (fl & (F_SLOWCAP | F_INTERNAL)) return SLOW_GAVE_UP;
     for (unsigned long long it = 0; it < steps; ++it) {
         unsigned long long base = p_start + 64ull * it;
         if (base > half) break;
@@ -216,15 +223,24 @@ static __device__ __noinline__ unsigned long long slow_pmin(unsigned long long n
         uint32_t m = __ballot_sync(GB_FULL_MASK, ok);
         if (m) return base + 2ull * (unsigned long long)(__ffs(m) - 1);
         if (it + 1 == steps) {
-            if (lane == 0) atomicOr(&ctrl->flags, F_SLOWCAP);
-            return 0;
+            if (lane == 0) atomicOr(flags, F_SLOWCAP);
+            return SLOW_GAVE_UP;
         }
     }
     if (lane == 0) {
-        atomicOr(&ctrl->flags, F_COUNTEREX);
-        atomicMax(&ctrl->ce_inv, ~n);
+        atomicOr(flags, F_COUNTEREX);
+        atomicMax(ce_inv, ~n);
     }
     return 0;
+}
+
+// Barrier of a group of NTH threads: the whole CTA (BAR = 0, __syncthreads)
+// or a named barrier shared by a subset of its warps (BAR = 1..15).
+template <int BAR, int NTH>
+__device__ __forceinline__ void group_sync()
+{
+    if (BAR == 0) __syncthreads();
+    else asm volatile("bar.sync %0, %1;" ::"n"(BAR), "n"(NTH) : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -529,9 +545,10 @@ __device__ __forceinline__ void bucket_pass(uint32_t *win, const WinGeom &g, con
 }
 
 // Build the whole window (passes 1-3).  Primes from index np_cap on are left
-// to the bucket entries [b0, b1) of ent (none when ent is null).  Ends with a
-// barrier.
-template <int WHEEL, int NT>
+// to the bucket entries [b0, b1) of ent (none when ent is null).  Run by
+// threads [0, NT) of the CTA, which meet at barrier BAR (0 = the whole CTA);
+// ends with that barrier.
+template <int WHEEL, int NT, int BAR = 0>
 __device__ __forceinline__ void build_window(uint32_t *win, const uint32_t *wpat, const WinGeom &g,
                                              const Tables &t, uint32_t np_cap = 0xffffffffu,
                                              const uint32_t *ent = nullptr,
@@ -539,13 +556,13 @@ __device__ __forceinline__ void build_window(uint32_t *win, const uint32_t *wpat
                                              Ctrl *ctrl = nullptr)
 {
     fill_pass<WHEEL, NT>(win, wpat, g, t.pat_lo, t.pat_hi, t.groups);
-    __syncthreads();
+    group_sync<BAR, NT>();
     uint32_t np = count_le_warp(t.primes, t.nprimes, isqrt_u64(g.q_hi));
     if (np > np_cap) np = np_cap;
     mark_pass<NT>(win, g, t, np);
     if (ent) bucket_pass<NT>(win, g, ent, b0, b1, ctrl);
     fixup_pass<WHEEL>(win, g, t.pat_hi);
-    __syncthreads();
+    group_sync<BAR, NT>();
 }
 
 // First odd multiple of p that is >= max(p^2, w), as a distance from w;

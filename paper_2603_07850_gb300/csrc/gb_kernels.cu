@@ -205,6 +205,9 @@ slice_sieve_kernel(unsigned long long half_abs, int neg, uint32_t j_end, uint32_
     for (uint32_t i = 4 * n4 + threadIdx.x; i < nw; i += NT) gwin[w0 + i] = win[i];
 }
 
+// Entry of the plain form's p_min array for an n whose slow path gave up.
+constexpr uint32_t PM_GAVE_UP = 0xffffffffu;
+
 // p_min for every n of a plain segment, read from the global window bitset.
 __global__ void __launch_bounds__(256)
 plain_search_kernel(const RangeParams *__restrict__ prm_g, const uint32_t *__restrict__ gwin,
@@ -226,14 +229,37 @@ plain_search_kernel(const RangeParams *__restrict__ prm_g, const uint32_t *__res
             const int src = __ffs(pend) - 1;
             pend &= pend - 1;
             const unsigned long long ns = __shfl_sync(GB_FULL_MASK, n, src);
-            unsigned long long ps = slow_pmin(ns, prm.p_slow_start, prm.slow_cap_log2, ctrl);
-            if (ps >= PMIN_LIMIT) {
+            unsigned long long ps = slow_pmin(ns, prm.p_slow_start, prm.slow_cap_log2, &ctrl->flags, &ctrl->ce_inv);
+            const bool gave_up = ps == SLOW_GAVE_UP;
+            if (!gave_up && ps >= PMIN_LIMIT) {
                 if (lane == 0) atomicOr(&ctrl->flags, F_OVERFLOW);
                 ps = PMIN_LIMIT - 1;
             }
-            if (lane == src) pm = (uint32_t)ps;
+            if (lane == src) pm = gave_up ? PM_GAVE_UP : (uint32_t)ps;
         }
         if (valid) pm_out[k] = pm;
+    }
+}
+
+// Plain form with the bit-parallel search: the CTAs take sub-tiles of 2^(
+// prm.tile_bits) n of the segment and search each in the segment's global
+// window bitset (sub-tile u starts at word u 2^(tile_bits - 5)) with the
+// persistent kernel's search and reduction, folding into the (zeroed)
+// records.  One launch replaces the per-n search and the reduce kernel.
+template <int NT, int BC>
+__global__ void __launch_bounds__(NT, 1)
+plain_bulk_kernel(RangeParams prm, unsigned long long tile_first, uint32_t nsub, Tables t,
+                  const uint32_t *__restrict__ gwin, DevRec *recs, Ctrl *ctrl)
+{
+    extern __shared__ __align__(16) uint32_t PRs[];
+    __shared__ RedScratch s;
+    for (uint32_t i = threadIdx.x; i < prm.k_words; i += NT) PRs[i] = t.PR[i];
+    if (threadIdx.x == 0) s.one = 1u;
+    __syncthreads();
+    for (uint32_t u = blockIdx.x; u < nsub; u += gridDim.x) {
+        search_tile<NT / 32, BC, 0>(prm, tile_first + u, t, PRs, gwin + ((size_t)u << (prm.tile_bits - 5)), s, recs,
+                                    ctrl, (int)(threadIdx.x >> 5), threadIdx.x);
+        __syncthreads();
     }
 }
 
@@ -262,6 +288,7 @@ plain_reduce_kernel(const RangeParams *__restrict__ prm_g, const uint32_t *__res
     __syncthreads();
     for (uint32_t k = ks + threadIdx.x; k < ke; k += NT) {
         const uint32_t p = pm[k];
+        if (p == PM_GAVE_UP) continue;                     // slow path gave up: the call fails
         if (p) a.add(p, kr0 + (k - ks), prm.p_max, s.hist);
         else a.ce = a.ce > ~(n_lo + 2ull * k) ? a.ce : ~(n_lo + 2ull * k);
     }
@@ -505,6 +532,8 @@ cudaError_t launch_set_params(cudaStream_t st, RangeParams *dst, const RangePara
     return cudaGetLastError();
 }
 
+const void *set_params_kernel_ptr() { return (const void *)set_params_kernel; }
+
 template <int WHEEL, int NT>
 static const void *slice_ptr() { return (const void *)slice_sieve_kernel<WHEEL, NT>; }
 
@@ -514,6 +543,23 @@ const void *persistent_kernel_ptr(int wheel, int nt, int bc)
     if (nt == 512) return persistent_ptr_512(wheel, bc);
     if (nt == 1024) return persistent_ptr_1024(wheel, bc);
     return nullptr;
+}
+
+const void *pipe_kernel_ptr(int wheel, int np, int nt, int bc)
+{
+    if (wheel != 13) return nullptr;
+    if (np == 8) return pipe_ptr_8(nt, bc);
+    if (np == 12 || np == 16) return pipe_ptr_16(np, nt, bc);
+    return nullptr;
+}
+
+cudaError_t launch_range_kernel(const void *fn, int nt, int grid, size_t smem, cudaStream_t st,
+                                const RangeParams *prm, const Tables &t, DevRec *recs, Ctrl *ctrl)
+{
+    if (!fn) return cudaErrorInvalidValue;
+    Tables tt = t;
+    void *args[] = {(void *)&prm, (void *)&tt, (void *)&recs, (void *)&ctrl};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(nt), args, smem, st);
 }
 
 const void *serve_kernel_ptr(int wheel, int nt, int bc)
@@ -577,6 +623,29 @@ cudaError_t launch_merge(cudaStream_t st, int grid, const RangeParams *prm, cons
 }
 
 size_t merge_part_bytes() { return sizeof(MergePart); }
+
+const void *plain_bulk_ptr(int bc)
+{
+    switch (bc) {
+        case 4: return (const void *)plain_bulk_kernel<1024, 4>;
+        case 6: return (const void *)plain_bulk_kernel<1024, 6>;
+        case 8: return (const void *)plain_bulk_kernel<1024, 8>;
+    }
+    return nullptr;
+}
+
+cudaError_t launch_plain_bulk(int bc, int grid, size_t smem, cudaStream_t st, const RangeParams &prm,
+                              unsigned long long tile_first, uint32_t nsub, const Tables &t, const uint32_t *gwin,
+                              DevRec *recs, Ctrl *ctrl)
+{
+    const void *fn = plain_bulk_ptr(bc);
+    if (!fn) return cudaErrorInvalidValue;
+    RangeParams p = prm;
+    Tables tt = t;
+    void *args[] = {(void *)&p, (void *)&tile_first, (void *)&nsub, (void *)&tt, (void *)&gwin, (void *)&recs,
+                    (void *)&ctrl};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(1024), args, smem, st);
+}
 
 cudaError_t launch_slice_sieve(int wheel, int nt, int grid, size_t smem, cudaStream_t st,
                                unsigned long long half_abs, int neg, uint32_t j_end, uint32_t Z,

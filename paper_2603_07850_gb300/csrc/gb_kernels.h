@@ -15,6 +15,15 @@ const void *persistent_ptr_256(int wheel, int bc);
 const void *persistent_ptr_512(int wheel, int bc);
 const void *persistent_ptr_1024(int wheel, int bc);
 const void *serve_ptr_512(int wheel, int bc);
+// pipelined kernel (window-building and searching warps, two window buffers):
+// np building warps out of nt threads; nullptr when not instantiated.
+// Defined in gb_pipe_8.cu / gb_pipe_16.cu; wheel 13 only.
+const void *pipe_kernel_ptr(int wheel, int np, int nt, int bc);
+const void *pipe_ptr_8(int nt, int bc);
+const void *pipe_ptr_16(int np, int nt, int bc);
+// launch a persistent or pipelined range kernel given by its pointer
+cudaError_t launch_range_kernel(const void *fn, int nt, int grid, size_t smem, cudaStream_t st,
+                                const RangeParams *prm, const Tables &t, DevRec *recs, Ctrl *ctrl);
 const void *serve_ptr_1024(int wheel, int bc);
 // serving work-list kernel; nullptr when (wheel, nt, bc) has no instantiation
 const void *serve_kernel_ptr(int wheel, int nt, int bc);
@@ -38,6 +47,12 @@ cudaError_t launch_slice_sieve(int wheel, int nt, int grid, size_t smem, cudaStr
 cudaError_t launch_plain_search(cudaStream_t st, int grid, const RangeParams *prm,
                                 const uint32_t *gwin, const uint32_t *PR, unsigned long long n_lo,
                                 uint32_t cnt, uint32_t *pm, Ctrl *ctrl);
+// plain form, bit-parallel search (1,024 threads, bc = 4, 6 or 8): sub-tiles
+// [tile_first, tile_first + nsub) of 2^prm.tile_bits n, window from gwin
+const void *plain_bulk_ptr(int bc);
+cudaError_t launch_plain_bulk(int bc, int grid, size_t smem, cudaStream_t st, const RangeParams &prm,
+                              unsigned long long tile_first, uint32_t nsub, const Tables &t, const uint32_t *gwin,
+                              DevRec *recs, Ctrl *ctrl);
 cudaError_t launch_plain_reduce(cudaStream_t st, const RangeParams *prm, const uint32_t *pm,
                                 unsigned long long k_seg0, unsigned long long n_lo, uint32_t cnt,
                                 uint32_t chunk, DevRec *recs, Ctrl *ctrl);
@@ -50,6 +65,8 @@ cudaError_t launch_table_compact(cudaStream_t st, const uint32_t *bits, uint32_t
 
 namespace gbk {
 cudaError_t launch_set_params(cudaStream_t st, RangeParams *dst, const RangeParams &p);
+// the kernel launch_set_params runs (its arguments: RangeParams *dst, RangeParams p)
+const void *set_params_kernel_ptr();
 // phase 0: count hits per tile + scan into off/cursor; phase 1: fill entries
 cudaError_t launch_bucket_prepass(cudaStream_t st, int grid, const RangeParams *prm, const Tables &t,
                                   uint32_t i0, unsigned long long t0, uint32_t nt, unsigned int *counts,

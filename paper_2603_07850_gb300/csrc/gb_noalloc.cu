@@ -37,6 +37,7 @@ namespace {
 // ---- fixed limits of the no-allocation entry point -------------------------
 constexpr uint32_t NA_TABLE_LIMIT = 1u << 20;     // base primes <= 2^20, so n < 2^40
 constexpr uint32_t NA_NPRIMES = 82024;            // odd primes <= 2^20 (pi(2^20) - 1)
+static_assert(NA_NPRIMES % 4 == 0, "the marking loads primes four at a time");
 constexpr uint32_t NA_MAX_KWORDS = 1024;          // P_max <= 2^16
 constexpr uint32_t NA_MAX_RECORDS = 8192;
 constexpr uint32_t NA_MERGE_GRID = 512;
@@ -66,9 +67,10 @@ __global__ void __launch_bounds__(1024) na_table_kernel(unsigned char *scr, unsi
     extern __shared__ uint32_t bits[];                // 2^14 words
     __shared__ uint32_t s_scan[1024];
     constexpr uint32_t NWORDS = NA_TABLE_LIMIT / 64;  // odd q < 2^20: 2^19 bits
-    for (uint32_t w = threadIdx.x; w < NWORDS; w += 1024) bits[w] = 0xffffffffu;
+    // bit 0 (q = 1) starts cleared, so no thread writes word 0 except by the
+    // atomic crossing-off below
+    for (uint32_t w = threadIdx.x; w < NWORDS; w += 1024) bits[w] = w ? 0xffffffffu : 0xfffffffeu;
     __syncthreads();
-    if (threadIdx.x == 0) bits[0] &= ~1u;             // q = 1
     for (uint32_t p = 3 + 2 * threadIdx.x; p < 1024; p += 2048) {
         bool prime = true;
         for (uint32_t d = 3; d * d <= p; d += 2)

@@ -48,14 +48,15 @@ struct LaneAcc {
     }
 };
 
-// CTA-wide reduction of the lanes' state into record r.  `whole` = the tile
-// owns the record (plain stores) instead of sharing it (atomics).
-template <int NT>
-__device__ __forceinline__ void reduce_to_record(LaneAcc &a, RedScratch &s, DevRec *rec,
-                                                 uint32_t n_cnt, bool whole, Ctrl *ctrl)
+// Reduction of the lanes' state over a group of NWARP warps into record r;
+// `warp` is the warp's index in the group (0 combines) and `gt` the thread's,
+// BAR the group's barrier (0 = the whole CTA).  `whole` = the tile owns the
+// record (plain stores) instead of sharing it (atomics).
+template <int NWARP, int BAR>
+__device__ __forceinline__ void reduce_group(LaneAcc &a, RedScratch &s, DevRec *rec, uint32_t n_cnt, bool whole,
+                                             Ctrl *ctrl, int warp)
 {
-    constexpr int NWARP = NT / 32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     uint32_t wmax = __reduce_max_sync(GB_FULL_MASK, a.mx);
     unsigned long long warg = warp_min_u64(a.mx == wmax ? a.arg : ~0ull);
     unsigned long long wsum = warp_sum_u64(a.sum), wws = warp_sum_u64(a.wsum);
@@ -79,7 +80,7 @@ __device__ __forceinline__ void reduce_to_record(LaneAcc &a, RedScratch &s, DevR
         s.mx[warp] = wmax; s.arg[warp] = warg; s.sum[warp] = wsum; s.wsum[warp] = wws;
         s.slow[warp] = wslow; s.ce[warp] = wce;
     }
-    __syncthreads();
+    group_sync<BAR, 32 * NWARP>();
     if (warp == 0) {
         uint32_t m = lane < NWARP ? s.mx[lane] : 0u;
         unsigned long long ar = lane < NWARP ? s.arg[lane] : ~0ull;
@@ -117,38 +118,48 @@ __device__ __forceinline__ void reduce_to_record(LaneAcc &a, RedScratch &s, DevR
     }
 }
 
-// One tile: build its window, search every n, reduce into its record(s).
-// Called by every thread of the CTA (it contains barriers).
-template <int WHEEL, int NT, int SEARCH_BC>
-__device__ __forceinline__ void run_tile(const RangeParams &prm, unsigned long long tile, const Tables &t,
-                                         const uint32_t *wpat, const uint32_t *PR, uint32_t *win,
-                                         RedScratch &s, DevRec *recs, Ctrl *ctrl)
+// CTA-wide reduction (every thread of an NT-thread CTA).
+template <int NT>
+__device__ __forceinline__ void reduce_to_record(LaneAcc &a, RedScratch &s, DevRec *rec,
+                                                 uint32_t n_cnt, bool whole, Ctrl *ctrl)
 {
-    constexpr int NWARP = NT / 32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t KW = prm.k_words;
-    const uint32_t rbits = prm.rec_bits < prm.tile_bits ? prm.rec_bits : prm.tile_bits;
-    const bool whole = prm.tile_bits >= prm.rec_bits;
-    const unsigned long long rmask = (1ull << prm.rec_bits) - 1ull;
-    // bit-parallel phase bound: candidates p <= bb (never above P_max or the
-    // search bound); the per-n phase starts at candidate index i_start
+    reduce_group<NT / 32, 0>(a, s, rec, n_cnt, whole, ctrl, (int)(threadIdx.x >> 5));
+}
+
+// Bit-parallel phase bound of a call: candidates p <= bb (never above P_max
+// or the search bound) resolve in the bulk phase; the per-n phase starts at
+// candidate index (bb + 1) / 2.
+template <int SEARCH_BC>
+__device__ __forceinline__ uint32_t bulk_bound(const RangeParams &prm)
+{
     const uint32_t ps_odd = (uint32_t)(prm.p_slow_start - 2ull);
     uint32_t bb = SEARCH_BC ? 64u * SEARCH_BC - 1u : 0u;
     if (bb > ps_odd) bb = ps_odd;
     if (bb > prm.p_max) bb = prm.p_max;
+    return bb;
+}
+
+// Search every n of a tile whose window is built, and reduce it into its
+// record(s).  Run by a group of NWARP warps (the whole CTA, BAR = 0, or the
+// searching warps of the pipelined kernel); `warp` and `gt` are the warp's
+// and the thread's index in the group.
+template <int NWARP, int SEARCH_BC, int BAR>
+__device__ __forceinline__ void search_tile(const RangeParams &prm, unsigned long long tile, const Tables &t,
+                                            const uint32_t *PR, const uint32_t *win, RedScratch &s,
+                                            DevRec *recs, Ctrl *ctrl, int warp, uint32_t gt)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t KW = prm.k_words;
+    const uint32_t rbits = prm.rec_bits < prm.tile_bits ? prm.rec_bits : prm.tile_bits;
+    const bool whole = prm.tile_bits >= prm.rec_bits;
+    const unsigned long long rmask = (1ull << prm.rec_bits) - 1ull;
+    const uint32_t bb = bulk_bound<SEARCH_BC>(prm);
     const uint32_t i_start = (bb + 1u) >> 1;
     const bool ball = SEARCH_BC && bb >= cand_last(SEARCH_BC ? SEARCH_BC : 1);
     const unsigned long long k0 = tile << prm.tile_bits;
     const unsigned long long left = prm.n_total - k0;
     const uint32_t cnt = left < (1ull << prm.tile_bits) ? (uint32_t)left : (1u << prm.tile_bits);
     const unsigned long long n_lo = prm.n0 + 2ull * k0;
-    const WinGeom g = tile_geom(n_lo, cnt, 32u * KW);
-    unsigned long long b0 = 0, b1 = 0;
-    if (prm.bk_ent) {
-        b0 = prm.bk_off[tile - prm.tile0];
-        b1 = prm.bk_off[tile - prm.tile0 + 1];
-    }
-    build_window<WHEEL, NT>(win, wpat, g, t, prm.bk_prime0, prm.bk_ent, b0, b1, ctrl);
 
     for (uint32_t ks = 0; ks < cnt; ks += (1u << rbits)) {
         const uint32_t ke = (cnt - ks) < (1u << rbits) ? cnt : ks + (1u << rbits);
@@ -157,9 +168,9 @@ __device__ __forceinline__ void run_tile(const RangeParams &prm, unsigned long l
         const unsigned long long kr0 = kg & rmask;
         LaneAcc a;
         a.reset();
-        if (threadIdx.x < HIST_BINS) s.hist[threadIdx.x] = 0u;
-        if (threadIdx.x == 0) { s.xslow = 0u; s.xce = 0ull; }
-        __syncthreads();
+        if (gt < HIST_BINS) s.hist[gt] = 0u;
+        if (gt == 0) { s.xslow = 0u; s.xce = 0ull; }
+        group_sync<BAR, 32 * NWARP>();
         if (SEARCH_BC == 0) {
             for (uint32_t g32 = (ks >> 5) + warp; (g32 << 5) < ke; g32 += NWARP) {
                 const uint32_t k = (g32 << 5) + lane;
@@ -172,14 +183,16 @@ __device__ __forceinline__ void run_tile(const RangeParams &prm, unsigned long l
                     const int src = __ffs(pend) - 1;
                     pend &= pend - 1;
                     const unsigned long long ns = __shfl_sync(GB_FULL_MASK, n, src);
-                    unsigned long long ps = slow_pmin(ns, prm.p_slow_start, prm.slow_cap_log2, ctrl);
-                    if (ps >= PMIN_LIMIT) {
+                    unsigned long long ps = slow_pmin(ns, prm.p_slow_start, prm.slow_cap_log2, &ctrl->flags,
+                                                      &ctrl->ce_inv);
+                    const bool gu = ps == SLOW_GAVE_UP;
+                    if (!gu && ps >= PMIN_LIMIT) {
                         if (lane == 0) atomicOr(&ctrl->flags, F_OVERFLOW);
                         ps = PMIN_LIMIT - 1;
                     }
-                    if (lane == src) {
-                        pm = (uint32_t)ps;
-                        if (!ps) a.ce = a.ce > ~ns ? a.ce : ~ns;
+                    if (lane == src) {                    // gave up: folded nowhere, the call fails
+                        pm = gu ? 0u : (uint32_t)ps;
+                        if (!gu && !ps) a.ce = a.ce > ~ns ? a.ce : ~ns;
                     }
                 }
                 if (valid && pm) a.add(pm, kr0 + (k - ks), prm.p_max, s.hist);
@@ -224,12 +237,43 @@ __device__ __forceinline__ void run_tile(const RangeParams &prm, unsigned long l
             a.hA = (unsigned long long)acc.h[0] | ((unsigned long long)acc.h[1] << 32);
             a.hB = (unsigned long long)acc.h[2] | ((unsigned long long)acc.h[3] << 32);
         }
-        reduce_to_record<NT>(a, s, rec, ke - ks, whole, ctrl);
+        reduce_group<NWARP, BAR>(a, s, rec, ke - ks, whole, ctrl, warp);
     }
 }
 
+// Build the window of one tile.  Run by threads [0, NT) of the CTA, which
+// meet at barrier BAR; ends with that barrier.
+template <int WHEEL, int NT, int BAR>
+__device__ __forceinline__ void build_tile(const RangeParams &prm, unsigned long long tile, const Tables &t,
+                                           const uint32_t *wpat, uint32_t *win, Ctrl *ctrl)
+{
+    const uint32_t KW = prm.k_words;
+    const unsigned long long k0 = tile << prm.tile_bits;
+    const unsigned long long left = prm.n_total - k0;
+    const uint32_t cnt = left < (1ull << prm.tile_bits) ? (uint32_t)left : (1u << prm.tile_bits);
+    const unsigned long long n_lo = prm.n0 + 2ull * k0;
+    const WinGeom g = tile_geom(n_lo, cnt, 32u * KW);
+    unsigned long long b0 = 0, b1 = 0;
+    if (prm.bk_ent) {
+        b0 = prm.bk_off[tile - prm.tile0];
+        b1 = prm.bk_off[tile - prm.tile0 + 1];
+    }
+    build_window<WHEEL, NT, BAR>(win, wpat, g, t, prm.bk_prime0, prm.bk_ent, b0, b1, ctrl);
+}
+
+// One tile: build its window, search every n, reduce into its record(s).
+// Called by every thread of the CTA (it contains barriers).
+template <int WHEEL, int NT, int SEARCH_BC>
+__device__ __forceinline__ void run_tile(const RangeParams &prm, unsigned long long tile, const Tables &t,
+                                         const uint32_t *wpat, const uint32_t *PR, uint32_t *win,
+                                         RedScratch &s, DevRec *recs, Ctrl *ctrl)
+{
+    build_tile<WHEEL, NT, 0>(prm, tile, t, wpat, win, ctrl);
+    search_tile<NT / 32, SEARCH_BC, 0>(prm, tile, t, PR, win, s, recs, ctrl, (int)(threadIdx.x >> 5), threadIdx.x);
+}
+
 // SEARCH_BC = 0: per-n search (one lane per n, 32 candidates per step).
-// SEARCH_BC = 2..4: bit-parallel search of the candidates p < 64 SEARCH_BC
+// SEARCH_BC = 4, 6, 8: bit-parallel search of the candidates p < 64 SEARCH_BC
 // (one lane per 32 n), the rest per n after warp compaction.
 // 512-thread CTAs are built for two per SM (64 registers a thread), so that with
 // tiles of at most 2^19 n one CTA can build its window while the other searches.
@@ -263,9 +307,75 @@ persistent_kernel(const RangeParams *__restrict__ prm_g, Tables t, DevRec *__res
     }
 }
 
+// ---------------------------------------------------------------------------
+// pipelined persistent kernel: warp-specialised, two window buffers
+// ---------------------------------------------------------------------------
+//
+// The window build is bound by shared-memory atomics and the search by
+// instruction issue, so the two overlap: warps [0, NP) (builders) sieve the
+// window of the CTA's next tile into one buffer while warps [NP, NP + NC)
+// (searchers) search the current tile in the other; the whole CTA meets once
+// per tile and the buffers swap.  The builders meet at named barrier 1, the
+// searchers at named barrier 2.  Tiles are claimed from the same device atomic
+// counter as the persistent kernel (one tile ahead), so records, order of
+// folding and results are identical.  Two windows must fit in shared memory:
+// tiles of at most 2^19 n at P_max = 2^16.
+template <int NP, int NC> constexpr int pipe_threads() { return 32 * (NP + NC); }
+
+template <int WHEEL, int NP, int NC, int SEARCH_BC>
+__global__ void __launch_bounds__(pipe_threads<NP, NC>(), 1)
+pipe_kernel(const RangeParams *__restrict__ prm_g, Tables t, DevRec *__restrict__ recs, Ctrl *ctrl)
+{
+    constexpr int NT = pipe_threads<NP, NC>();
+    constexpr int NPT = 32 * NP, NCT = 32 * NC;
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ RedScratch s;
+    __shared__ unsigned long long s_tile[2];
+    constexpr uint32_t WP = pattern_block_words<WHEEL>();
+    if (threadIdx.x == 0) { s.prm = *prm_g; s.one = 1u; }
+    const RangeParams &prm = s.prm;
+    const uint32_t KW = prm_g->k_words;
+    const uint32_t WW = pipe_window_words(prm_g->tile_bits, KW);
+    uint32_t *wpat = smem;
+    uint32_t *PR = wpat + WP;
+    // buffer b is win0 + b WW: computed from the shared-memory base (an array
+    // of the two pointers would hide that they point to shared memory, and
+    // every access would become a generic one)
+    uint32_t *win0 = PR + ((KW + 3) & ~3u);
+    build_wheel_pattern<WHEEL, NT>(wpat);
+    for (uint32_t i = threadIdx.x; i < KW; i += NT) PR[i] = t.PR[i];
+    const int warp = (int)(threadIdx.x >> 5);
+    const bool builder = warp < NP;
+    if (threadIdx.x == 0)
+        s_tile[0] = prm_g->tile0 + (prm_g->claim ? atomicAdd_system(prm_g->claim, 1ull) : atomicAdd(&ctrl->tile_ctr, 1ull));
+    __syncthreads();
+    if (builder && s_tile[0] < prm.tile_end) build_tile<WHEEL, NPT, 1>(prm, s_tile[0], t, wpat, win0, ctrl);
+    __syncthreads();
+    for (uint32_t k = 0;; k++) {
+        const unsigned long long tile = s_tile[k & 1u];
+        if (tile >= prm.tile_end) break;
+        if (builder) {
+            if (threadIdx.x == 0)
+                s_tile[(k + 1u) & 1u] =
+                    prm.tile0 + (prm.claim ? atomicAdd_system(prm.claim, 1ull) : atomicAdd(&ctrl->tile_ctr, 1ull));
+            group_sync<1, NPT>();
+            const unsigned long long next = s_tile[(k + 1u) & 1u];
+            if (next < prm.tile_end)
+                build_tile<WHEEL, NPT, 1>(prm, next, t, wpat, win0 + ((k & 1u) ? 0u : WW), ctrl);
+        } else {
+            const uint32_t gt = threadIdx.x - NPT;
+            search_tile<NC, SEARCH_BC, 2>(prm, tile, t, PR, win0 + ((k & 1u) ? WW : 0u), s, recs, ctrl, warp - NP, gt);
+            if (gt == 0 && prm.progress) atomicAdd_system(prm.progress, 1ull);
+        }
+        __syncthreads();
+    }
+    (void)NCT;
+}
+
 // Serving: CTAs claim work items (slot, tile) of the admitted requests from a
 // device counter, so the tiles of many requests share one persistent launch;
-// each tile folds into its request's record with atomics.
+// each tile folds into its request's record with atomics, and raises its
+// status flags and counterexample in the request's own control block.
 template <int WHEEL, int NT, int SEARCH_BC>
 __global__ void __launch_bounds__(NT, min_ctas<NT>())
 serve_kernel(const unsigned long long *__restrict__ items, unsigned long long n_items, SlotDev *slots,
@@ -294,7 +404,7 @@ serve_kernel(const unsigned long long *__restrict__ items, unsigned long long n_
         const unsigned long long item = items[idx];
         const unsigned long long slot = item >> SERVE_SLOT_SHIFT;
         const unsigned long long tile = item & ((1ull << SERVE_SLOT_SHIFT) - 1ull);
-        run_tile<WHEEL, NT, SEARCH_BC>(s.prm, tile, t, wpat, PR, win, s, &slots[slot].acc, ctrl);
+        run_tile<WHEEL, NT, SEARCH_BC>(s.prm, tile, t, wpat, PR, win, s, &slots[slot].acc, &slots[slot].ctl);
     }
 }
 

@@ -197,7 +197,11 @@ __device__ __forceinline__ uint32_t bulk_word(const uint32_t *win, uint32_t w, u
     uint32_t B0 = ~valid, B1 = 0, B2 = 0, B3 = 0, B4 = 0, B5 = 0, B6 = 0, B7 = 0, B8 = 0;
 #pragma unroll
     for (int c = 0; c < BC; c++) {
-        const uint32_t lo = win[w + KW - 1 - c], hi = win[w + KW - c];
+        // a chunk past the window's K bits holds no candidate <= bb (only
+        // possible when !ALL, with a search bound below 64 BC): it loads
+        // nothing, so no index runs below the window
+        const bool cin = ALL || (uint32_t)c < KW;
+        const uint32_t lo = cin ? win[w + KW - 1 - c] : 0u, hi = cin ? win[w + KW - c] : 0u;
 #pragma unroll
         for (int h = 0; h < 2; h++) {
             const uint32_t g = 2u * c + h;                // p in [32 g, 32 g + 32)
@@ -298,14 +302,15 @@ __device__ __forceinline__ void tail_one(const uint32_t *win, const uint32_t *PR
         const int src = __ffs(pend) - 1;
         pend &= pend - 1;
         const unsigned long long ns = __shfl_sync(GB_FULL_MASK, n, src);
-        unsigned long long ps = slow_pmin(ns, prm.p_slow_start, prm.slow_cap_log2, ctrl);
-        if (ps >= PMIN_LIMIT) {
+        unsigned long long ps = slow_pmin(ns, prm.p_slow_start, prm.slow_cap_log2, &ctrl->flags, &ctrl->ce_inv);
+        const bool gave_up = ps == SLOW_GAVE_UP;           // the call fails; the n is folded nowhere
+        if (!gave_up && ps >= PMIN_LIMIT) {
             if (lane == 0) atomicOr(&ctrl->flags, F_OVERFLOW);
             ps = PMIN_LIMIT - 1;
         }
         if ((int)lane == src) {
-            pm = (uint32_t)ps;
-            if (!ps) atomicMax(ss.ce, ~ns);
+            pm = gave_up ? 0u : (uint32_t)ps;
+            if (!gave_up && !ps) atomicMax(ss.ce, ~ns);
         }
     }
     if (act && pm) {

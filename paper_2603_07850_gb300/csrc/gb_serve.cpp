@@ -209,9 +209,8 @@ void worker_loop()
         if (!inflight.empty() && (inflight.size() == 2 || drain || batch_items.empty())) {
             Batch b = inflight.front();
             inflight.pop_front();
-            unsigned int flags = 0;
             // no context lock while waiting; bounded by the timeout_ms option
-            const int rc = ctx_serve_wait(b.buf, &flags, ctx_option("timeout_ms"));
+            const int rc = ctx_serve_wait(b.buf, ctx_option("timeout_ms"));
             if (rc == GB_ETIMEOUT) {
                 // report at once: every admitted and every pending request fails.
                 // Their slots are taken now: gb_poll may erase a finished request.
@@ -230,9 +229,8 @@ void worker_loop()
                     s.cv_done.notify_all();
                 }
                 // then let the device finish before any slot or buffer is reused
-                unsigned int f;
-                ctx_serve_wait(b.buf, &f, -1);
-                for (auto &o : inflight) ctx_serve_wait(o.buf, &f, -1);
+                ctx_serve_wait(b.buf, -1);
+                for (auto &o : inflight) ctx_serve_wait(o.buf, -1);
                 inflight.clear();
                 std::lock_guard<std::mutex> lk(s.mu);
                 for (auto &h : held) {
@@ -255,7 +253,7 @@ void worker_loop()
                 }
                 gb_result res{};
                 int frc = rc;
-                if (frc == GB_OK) frc = ctx_serve_fetch(slot, sp, flags, &res);
+                if (frc == GB_OK) frc = ctx_serve_fetch(slot, sp, &res);
                 if (frc != GB_OK) { memset(&res, 0, sizeof res); res.status = frc; }
                 out.emplace_back(id, res);
             }
@@ -272,10 +270,7 @@ void worker_loop()
     }
     // stopping: let in-flight batches finish before the context goes away
     std::lock_guard<std::recursive_mutex> ck(ctx_mutex());
-    for (auto &b : inflight) {
-        unsigned int f;
-        ctx_serve_wait(b.buf, &f, -1);
-    }
+    for (auto &b : inflight) ctx_serve_wait(b.buf, -1);
 }
 
 int ensure_worker()

@@ -29,8 +29,9 @@ void ctx_serve_release_slot(int slot);
 unsigned long long *ctx_serve_items(int buf);
 int ctx_serve_launch(int buf, size_t n);
 // timeout_ms < 0: wait without bound
-int ctx_serve_wait(int buf, unsigned int *flags, int64_t timeout_ms);
-int ctx_serve_fetch(int slot, const ServePlan &sp, unsigned int flags, gb_result *out);
+int ctx_serve_wait(int buf, int64_t timeout_ms);
+// a finished request's result, its status from its own flags
+int ctx_serve_fetch(int slot, const ServePlan &sp, gb_result *out);
 size_t ctx_serve_slot_bytes();
 // provided by gb_serve.cpp
 void serve_stop();

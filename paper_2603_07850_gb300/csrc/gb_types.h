@@ -62,14 +62,25 @@ struct __align__(16) RangeParams {
 
 // Serving: one admitted request.  Its params have rec_bits = 40 so the whole
 // request folds into the single record acc (requests have fewer than 2^40 n).
+// ctl holds the request's own status flags and counterexample, accumulated
+// over every batch that runs one of its tiles (its tile counter is unused).
 struct __align__(16) SlotDev {
     RangeParams prm;
     DevRec acc;
+    Ctrl ctl;
 };
 constexpr int SERVE_SLOT_SHIFT = 40;       // work item = (slot << 40) | tile
 
+// Words of one tile window in shared memory: 2^tile_bits + 32 k_words bits,
+// two spare words for the funnel shifts, rounded up to 16 bytes.
+__host__ __device__ constexpr uint32_t pipe_window_words(uint32_t tile_bits, uint32_t k_words)
+{
+    return (((1u << tile_bits) + 32u * k_words) / 32u + 2u + 3u) & ~3u;
+}
+
 // Read-only device tables shared by every kernel.
 struct Tables {
+    // both arrays are padded with zeros to a multiple of four entries
     const uint32_t *primes;            // odd primes ascending, primes[0] = 3
     const unsigned long long *recip;   // floor((2^64 - 1) / p)
     const uint32_t *PR;                // bit-reversed candidate words

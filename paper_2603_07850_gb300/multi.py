@@ -58,15 +58,19 @@ def merge_results(parts: list[dict]) -> dict:
     return out
 
 
-def merge_record_sets(sets):
+def merge_record_sets(sets, n_total: int | None = None):
     """Merge the record arrays (SEG_DTYPE, same range and seg_bits) of callers
     that each verified part of the tiles of one range, as from
     gb_verify_range_claimed: counts, sums (mod 2^64) and histograms add, the
     largest p_min wins with its smallest n, the smallest counterexample wins.
-    The result equals the records of one call over the whole range."""
+    The result equals the records of one call over the whole range.  With
+    n_total (the range's number of even n) the merged counts must add up to
+    it: a tile verified twice or never makes the merge fail."""
     import numpy as np
     sets = [s for s in sets if len(s)]
     if not sets:
+        if n_total:
+            raise ValueError(f"no records, but the range holds {n_total} even n")
         return []
     out = sets[0].copy()
     for s in sets[1:]:
@@ -82,6 +86,8 @@ def merge_record_sets(sets):
         out["argmax_n"] = np.where(better, s["argmax_n"], out["argmax_n"])
         ce_a, ce_b = out["counterexample_n"], s["counterexample_n"]
         out["counterexample_n"] = np.where((ce_a == 0) | ((ce_b != 0) & (ce_b < ce_a)), ce_b, ce_a)
+    if n_total is not None and int(out["n_count"].sum()) != n_total:
+        raise ValueError(f"merged records hold {int(out['n_count'].sum())} even n, the range {n_total}")
     return out
 
 

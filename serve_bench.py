@@ -57,25 +57,18 @@ def run(gb, reqs, rate):
     return results
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--requests", type=int, default=10_000)
-    ap.add_argument("--capacity-requests", type=int, default=2000)
-    ap.add_argument("--load", type=float, default=0.7)
-    ap.add_argument("--budget-mb", type=int, default=8192)
-    ap.add_argument("--oracle-sample", type=float, default=0.01)
-    args = ap.parse_args()
-
-    from paper_2603_07850_gb300 import binding as gb, build
+def measure(gb, requests: int = 10_000, capacity_requests: int = 2000, load: float = 0.7,
+            budget_mb: int = 8192, oracle_sample: float = 0.01) -> dict:
+    """Capacity closed-loop, then the seeded Poisson stream at load x capacity,
+    then the oracle on a seeded sample; returns the summary dict.  Runs on a
+    fresh library context (gb_init) and shuts it down."""
     from paper_2603_07850_gb300 import workloads as W
-    build.build()
-    gb.load()
     gb.gb_init(1 << 16, 20)
-    gb.gb_set_option("mem_budget_mb", args.budget_mb)
+    gb.gb_set_option("mem_budget_mb", budget_mb)
     gb.gb_set_option("base_limit", 32_000_000)          # base primes kept resident
 
     # capacity: closed loop on a prefix of the stream
-    cap_reqs = W.serving_stream(count=args.capacity_requests, rate_per_s=1.0, seed=W.SEED_C4)
+    cap_reqs = W.serving_stream(count=capacity_requests, rate_per_s=1.0, seed=W.SEED_C4)
     t = time.perf_counter()
     res = run(gb, cap_reqs, None)
     cap_s = time.perf_counter() - t
@@ -84,8 +77,8 @@ def main():
     cap_n = sum(r["n_count"] for _, r in res)
 
     # the Poisson stream at load x capacity
-    rate = args.load * capacity
-    reqs = W.serving_stream(count=args.requests, rate_per_s=rate, seed=W.SEED_C4)
+    rate = load * capacity
+    reqs = W.serving_stream(count=requests, rate_per_s=rate, seed=W.SEED_C4)
     t = time.perf_counter()
     res = run(gb, reqs, rate)
     wall = time.perf_counter() - t
@@ -99,7 +92,7 @@ def main():
     import oracle
     rng = W.SplitMix64(W.SEED_C4 + 1)
     picked = [i for i in range(len(reqs))
-              if rng.uniform() < args.oracle_sample and reqs[i].hi - reqs[i].lo <= 10**7]
+              if rng.uniform() < oracle_sample and reqs[i].hi - reqs[i].lo <= 10**7]
     base = oracle.primes_upto(32_000_000)
     mism = 0
     for i in picked:
@@ -115,17 +108,34 @@ def main():
         mism += 0 if ok else 1
     stats = gb.gb_stats()
     gb.gb_shutdown()
-    print(json.dumps({
-        "metric": "serving latency at 70% load", "requests": len(reqs), "load": args.load,
+    return {
+        "metric": f"serving latency at {round(100 * load)}% load", "requests": len(reqs), "load": load,
         "capacity_req_per_s": capacity, "capacity_even_n_per_s": cap_n / cap_s,
+        "capacity_requests": len(cap_reqs),
         "arrival_rate_req_per_s": rate, "p50_s": percentile(lat, 0.5), "p99_s": percentile(lat, 0.99),
         "mean_s": sum(lat) / len(lat), "max_s": max(lat),
         "throughput_even_n_per_s": n_total / ((last - first) * 1e-9),
-        "wall_s": wall, "failed": len(bad), "budget_mb": args.budget_mb,
+        "wall_s": wall, "failed": len(bad), "budget_mb": budget_mb,
         "oracle_checked": len(picked), "oracle_mismatches": mism,
         "kernel_launches": stats["kernel_launches"], "data": "synthetic",
         "workload": "lo uniform even in [4, 1e15), width log-uniform in [1e4, 1e10], seed 0xC4",
-    }), flush=True)
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--requests", type=int, default=10_000)
+    ap.add_argument("--capacity-requests", type=int, default=2000)
+    ap.add_argument("--load", type=float, default=0.7)
+    ap.add_argument("--budget-mb", type=int, default=8192)
+    ap.add_argument("--oracle-sample", type=float, default=0.01)
+    args = ap.parse_args()
+
+    from paper_2603_07850_gb300 import binding as gb, build
+    build.build()
+    gb.load()
+    out = measure(gb, args.requests, args.capacity_requests, args.load, args.budget_mb, args.oracle_sample)
+    print(json.dumps(out), flush=True)
 
 
 if __name__ == "__main__":

@@ -54,7 +54,7 @@ def test_dealt_tiles_merge_to_the_whole_range(lo, hi, seg_bits, tile_bits, seed)
     owner = [rng.randrange(3) for _ in range(ntiles)]
     parts = [caller_records(lo, hi, seg_bits, tile_bits, [t for t in range(ntiles) if owner[t] == c])
              for c in range(3)]
-    merged = multi.merge_record_sets(parts)
+    merged = multi.merge_record_sets(parts, n_total=n_total)
     st, want, _, _ = oracle.pmin_range(lo, hi, p_max=1 << 16, seg_bits=seg_bits)
     assert len(merged) == len(want)
     for r in range(len(want)):
@@ -63,3 +63,19 @@ def test_dealt_tiles_merge_to_the_whole_range(lo, hi, seg_bits, tile_bits, seed)
 
 def test_merge_of_nothing():
     assert multi.merge_record_sets([]) == []
+
+
+def test_a_tile_taken_twice_or_never_fails_the_merge():
+    lo, hi, seg_bits, tile_bits = 10**6, 10**6 + 2 * 5000 + 1, 12, 10
+    n_total = W.num_even(lo, hi)
+    ntiles = (n_total + (1 << tile_bits) - 1) >> tile_bits
+    every = list(range(ntiles))
+    twice = [caller_records(lo, hi, seg_bits, tile_bits, every),
+             caller_records(lo, hi, seg_bits, tile_bits, [0])]
+    with pytest.raises(ValueError):
+        multi.merge_record_sets(twice, n_total=n_total)
+    never = [caller_records(lo, hi, seg_bits, tile_bits, every[1:])]
+    with pytest.raises(ValueError):
+        multi.merge_record_sets(never, n_total=n_total)
+    assert multi.merge_record_sets([caller_records(lo, hi, seg_bits, tile_bits, every)],
+                                   n_total=n_total) is not None

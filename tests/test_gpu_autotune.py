@@ -6,7 +6,8 @@ import pytest
 
 pytestmark = pytest.mark.gpu
 
-KEYS = ("tile_bits", "threads", "search_chunks", "pattern_max", "search_pmax", "tier_b_min", "wheel")
+KEYS = ("tile_bits", "threads", "search_chunks", "pattern_max", "search_pmax", "tier_b_min", "wheel",
+        "builder_warps")
 
 
 def test_autotune_keeps_results_and_caches(tmp_path, monkeypatch):

@@ -45,10 +45,11 @@ def run(gb, lo, hi, p_max, seg_bits, **opts):
     (64, 3, 14),          # almost every prime bucketed
     (0, 2048, 16),        # the automatic bound (window span)
 ])
-def test_buckets_match_oracle(gb, bucket_min, chunk, tile_bits):
+@pytest.mark.parametrize("builders", [0, 8], ids=["persistent", "pipelined"])
+def test_buckets_match_oracle(gb, bucket_min, chunk, tile_bits, builders):
     lo, hi = 10**13 + 2, 10**13 + 2 * 10**7 + 7
     recs, agg = run(gb, lo, hi, 1 << 16, 12, tile_bits=tile_bits, bucket_min=bucket_min,
-                    bucket_chunk_tiles=chunk)
+                    bucket_chunk_tiles=chunk, builder_warps=builders)
     st, orecs, _, _ = oracle.pmin_range(lo, hi, p_max=1 << 16, seg_bits=12)
     d = recutil.diff(recs, orecs)
     assert not d, d
@@ -73,9 +74,11 @@ def test_high_offset_subwindows(gb, name, lo, hi, rec):
 
 
 @pytest.mark.parametrize("cfg", [W.C3A, W.C3B], ids=lambda c: c.name)
-def test_high_offset_full_windows(gb, cfg):
+@pytest.mark.parametrize("kopts", [{"builder_warps": 0, "tile_bits": 20}, {"builder_warps": 8, "tile_bits": 19}],
+                         ids=["persistent", "pipelined"])
+def test_high_offset_full_windows(gb, cfg, kopts):
     g = json.load(open(os.path.join(GOLDEN, "c3_windows.json")))[cfg.name]
-    recs, agg = run(gb, cfg.lo, cfg.hi, cfg.p_max, 20)
+    recs, agg = run(gb, cfg.lo, cfg.hi, cfg.p_max, 20, **kopts)
     n0 = W.first_even(cfg.lo)
     for w in g["windows"]:
         r = (w["lo"] - n0) // 2 >> 20
@@ -116,11 +119,12 @@ def test_published_pmin_record(gb):
     assert without_nslow(r_win) == without_nslow(r_slow)
 
 
-def test_top_of_u64_range(gb):
+@pytest.mark.parametrize("kopts", [{}, {"builder_warps": 16, "tile_bits": 18}], ids=["persistent", "pipelined"])
+def test_top_of_u64_range(gb, kopts):
     # hi = 2^64 - 1 includes n = 2^64 - 2; nothing may wrap
     e = W.C3_EDGE
     g = json.load(open(os.path.join(GOLDEN, "c3_windows.json")))[e.name]["windows"][0]
-    recs, agg = run(gb, e.lo, e.hi, e.p_max, 20)
+    recs, agg = run(gb, e.lo, e.hi, e.p_max, 20, **kopts)
     assert len(recs) == 1 and int(recs[0]["n_count"]) == 1 << 20
     assert recutil.canon(recs[0]) == recutil.canon(g["record"])
     assert agg["argmax_n"] <= (1 << 64) - 2

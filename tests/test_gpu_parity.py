@@ -107,10 +107,43 @@ def test_kernel_options_do_not_change_records(gb, opts):
     check_against_oracle(gb, 4, 2_000_001, 1 << 16, 14, tile_bits=17, **opts)
 
 
+# the pipelined kernel (window-building and searching warps, two window
+# buffers) in every instantiated shape and search form
+@pytest.mark.parametrize("opts", [
+    {"builder_warps": 8},
+    {"builder_warps": 12, "search_chunks": 6},
+    {"builder_warps": 16},
+    {"builder_warps": 8, "threads": 768, "search_chunks": 6},
+    {"builder_warps": 8, "search_chunks": 0},
+    {"builder_warps": 16, "search_chunks": 0, "tier_b_min": 64},
+    {"builder_warps": 8, "search_chunks": 4},
+    {"builder_warps": 16, "search_chunks": 8},
+    {"builder_warps": 8, "search_chunks": 6, "use_graph": 0},
+    {"builder_warps": 16, "search_chunks": 6, "search_pmax": 300},  # bound below the last chunk
+    {"builder_warps": 8, "search_chunks": 8, "search_pmax": 40},    # two words of candidates
+])
+def test_pipelined_kernel_matches_oracle(gb, opts):
+    check_against_oracle(gb, 4, 2_000_001, 1 << 16, 14, tile_bits=17, **opts)
+
+
+@pytest.mark.parametrize("lo,hi,seg_bits,tile_bits", [
+    (4, 3_000_001, 15, 19),        # records inside one tile
+    (4, 3_000_001, 18, 12),        # tiles inside one record (atomic merge)
+    (0, 2_100_000, 16, 16),        # tile == record
+    (1001, 777_777, 9, 10),        # odd lo, small records, ragged tail
+    (123_456_788, 125_000_001, 17, 14),
+])
+def test_pipelined_small_ranges(gb, lo, hi, seg_bits, tile_bits):
+    recs, agg, orecs = check_against_oracle(gb, lo, hi, 1 << 16, seg_bits, tile_bits=tile_bits,
+                                            builder_warps=8, search_chunks=6)
+    check_aggregate(agg, orecs, lo)
+
+
 @pytest.mark.parametrize("p_max", [2, 3, 64, 100, 1 << 12, 1 << 20])
-def test_pmax_changes_only_nslow(gb, p_max):
+@pytest.mark.parametrize("builders", [0, 8], ids=["persistent", "pipelined"])
+def test_pmax_changes_only_nslow(gb, p_max, builders):
     # candidates above P_max go through the GPU slow path; results identical
-    check_against_oracle(gb, 4, 400_001, p_max, 12, tile_bits=14)
+    check_against_oracle(gb, 4, 400_001, p_max, 12, tile_bits=14, builder_warps=builders)
 
 
 @pytest.mark.parametrize("lo,hi", [
@@ -125,10 +158,21 @@ def test_tiny_and_empty_ranges(gb, lo, hi):
     check_aggregate(agg, orecs, lo)
 
 
-def test_plain_form_matches_oracle(gb):
+@pytest.mark.parametrize("pbc", [0, 4, 6, 8], ids=lambda v: f"plain_search_chunks{v}")
+def test_plain_form_matches_oracle(gb, pbc):
     recs, agg, orecs = check_against_oracle(gb, 4, 3_000_001, 1 << 16, 15, plain=True,
-                                            plain_seg_bits=20, plain_slice_bits=16)
+                                            plain_seg_bits=20, plain_slice_bits=16,
+                                            plain_search_chunks=pbc)
     check_aggregate(agg, orecs, 4)
+
+
+@pytest.mark.parametrize("seg_bits,plain_seg_bits", [(12, 21), (18, 22), (20, 24)])
+def test_plain_bit_parallel_ragged_segments(gb, seg_bits, plain_seg_bits):
+    # several segments, sub-tiles sharing and owning records, ragged last segment
+    recs, agg, orecs = check_against_oracle(gb, 10**9 + 2, 10**9 + 2 * 9_000_001, 1 << 16, seg_bits,
+                                            plain=True, plain_seg_bits=plain_seg_bits,
+                                            plain_search_chunks=6)
+    check_aggregate(agg, orecs, 10**9 + 2)
 
 
 # ---------------------------------------------------------------------------
@@ -136,10 +180,14 @@ def test_plain_form_matches_oracle(gb):
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("cfg", [W.C0, W.C0_PMAX64], ids=lambda c: c.name)
-@pytest.mark.parametrize("plain", [False, True], ids=["persistent", "plain"])
-def test_c0_full_range(gb, cfg, plain):
+@pytest.mark.parametrize("form", [{"plain": False}, {"plain": True},
+                                  {"plain": True, "plain_search_chunks": 6}],
+                         ids=["persistent", "plain", "plain_bitparallel"])
+def test_c0_full_range(gb, cfg, form):
+    plain = form["plain"]
+    opts = {k: v for k, v in form.items() if k != "plain"}
     recs, agg, orecs = check_against_oracle(gb, cfg.lo, cfg.hi, cfg.p_max, cfg.seg_bits,
-                                            plain=plain)
+                                            plain=plain, **opts)
     check_aggregate(agg, orecs, cfg.lo)
     assert len(recs) == 191
     if cfg.p_max == 64:
@@ -150,9 +198,14 @@ def test_c0_full_range(gb, cfg, plain):
 # full 10^10 range against the stored oracle digest
 # ---------------------------------------------------------------------------
 
-def test_c1_full_range_digest(gb):
+KERNELS = [{"builder_warps": 0, "tile_bits": 20}, {"builder_warps": 8, "tile_bits": 19}]
+KERNEL_IDS = ["persistent", "pipelined"]
+
+
+@pytest.mark.parametrize("kopts", KERNELS, ids=KERNEL_IDS)
+def test_c1_full_range_digest(gb, kopts):
     g = json.load(open(os.path.join(GOLDEN, "c1_digest.json")))
-    init(gb, g["p_max"], g["seg_bits"])
+    init(gb, g["p_max"], g["seg_bits"], **kopts)
     recs, agg = gpu_records(gb, g["lo"], g["hi"])
     assert len(recs) == g["n_records"]
     assert recutil.digest(recs) == g["sha256"]
@@ -165,9 +218,10 @@ def test_c1_full_range_digest(gb):
 # full 10^12 range: 64 seeded records and the global max against the oracle
 # ---------------------------------------------------------------------------
 
-def test_c2_full_range_sampled(gb):
+@pytest.mark.parametrize("kopts", KERNELS, ids=KERNEL_IDS)
+def test_c2_full_range_sampled(gb, kopts):
     g = json.load(open(os.path.join(GOLDEN, "c2_samples.json")))
-    init(gb, g["p_max"], g["seg_bits"])
+    init(gb, g["p_max"], g["seg_bits"], **kopts)
     recs, agg = gpu_records(gb, g["lo"], g["hi"])
     for s in g["records"]:
         assert recutil.canon(recs[s["index"]]) == recutil.canon(s["record"]), s["index"]

@@ -2,7 +2,8 @@
 
 Records depend only on their own range, so a range verified in pieces that
 split at record boundaries gives the same records, and merged aggregate, as
-one call: an interrupted run resumes from its first unfinished record.
+one call: an interrupted run resumes from its first unfinished record.  The
+records around the cut, and seeded others, are checked against the oracle.
 """
 import threading
 import time
@@ -10,6 +11,8 @@ import time
 import numpy as np
 import pytest
 
+import oracle
+import recutil
 from paper_2603_07850_gb300 import multi
 from paper_2603_07850_gb300 import workloads as W
 
@@ -37,10 +40,20 @@ def test_progress_is_readable_while_a_call_runs(gb):
         seen.append(gb.gb_progress())
         time.sleep(0.01)
     th.join()
-    done, total = gb.gb_progress()
-    assert total == (W.num_even(lo, hi) + (1 << 20) - 1) >> 20 and done == total
-    assert any(0 < d < t for d, t in seen), seen[:5]
-    assert all(a[0] <= b[0] for a, b in zip(seen, seen[1:]))   # never goes back
+    last = gb.gb_progress()
+    tile_n = 1 << gb.gb_get_option("tile_bits")
+    n_total = W.num_even(lo, hi)
+    assert last["tiles_total"] == (n_total + tile_n - 1) // tile_n
+    assert last["tiles_done"] == last["tiles_total"]
+    assert last["n_done"] == last["n_total"] == n_total and last["eta_s"] == 0.0
+    mid = [p for p in seen if 0 < p["tiles_done"] < p["tiles_total"]]
+    assert mid, seen[:5]
+    for p in mid:
+        # a rate and a time left are reported while the call runs
+        assert p["n_done"] == p["tiles_done"] * tile_n and p["n_total"] == n_total
+        assert p["n_per_s"] > 0 and p["eta_s"] > 0
+        assert abs(p["eta_s"] - (n_total - p["n_done"]) / p["n_per_s"]) < 1e-6 * max(1.0, p["eta_s"])
+    assert all(a["tiles_done"] <= b["tiles_done"] for a, b in zip(seen, seen[1:]))   # never goes back
     assert out["r"]["status"] == 0
 
 
@@ -57,3 +70,11 @@ def test_resume_from_a_record_boundary(gb):
     merged = multi.merge_results([agg_a, agg_b])
     for k in ("n_first", "n_count", "max_pmin", "argmax_n", "sum_pmin", "wsum_pmin", "hist", "n_slow"):
         assert merged[k] == agg[k], k
+    # the records on both sides of the cut, the ragged last one and seeded
+    # others equal the oracle's
+    cfg = W.RangeConfig("resume", lo, hi, 1 << 16, seg, 0, "")
+    rs = np.concatenate([a, b])
+    for r in sorted({cut - 1, cut, nrec - 1, *W.sample_records(cfg, 3, 0xF3)}):
+        ra, rb = W.record_bounds(lo, hi, seg, r)
+        st, orecs, _, _ = oracle.pmin_range(ra, rb, p_max=1 << 16, seg_bits=seg)
+        assert st == 0 and recutil.canon(rs[r]) == recutil.canon(orecs[0]), r

@@ -122,3 +122,42 @@ def test_admission_budget_and_empty_requests(gb):
     st, r = gb.gb_poll(t, -1)
     assert st == 0 and r["n_count"] == 500
     assert gb.gb_stats()["requests_rejected"] == 1
+
+
+@pytest.mark.parametrize("small_first", [True, False], ids=["small_first", "big_first"])
+def test_request_status_is_its_own(gb, small_first):
+    # P_max = 2 sends every n >= 6 to the slow path; a cap of 2^7 = 64
+    # candidates (p <= 129) resolves every n below 1,000 (largest p_min 73)
+    # but not n = 5,372 (p_min above 129, found by the oracle).  With 1,024-n
+    # tiles [5300, 7400) is two tiles and only the first fails; with two tiles
+    # per batch the small request shares a batch with that tile or with the
+    # clean one, depending on arrival.
+    gb.gb_init(2, 20)
+    for k, v in {"slow_cap": 7, "tile_bits": 10, "serve_batch_tiles": 2}.items():
+        gb.gb_set_option(k, v)
+    small_alone = strip(gb.gb_verify_range(4, 1000))
+    assert small_alone["status"] == 0
+    order = [(4, 1000), (5300, 7400)] if small_first else [(5300, 7400), (4, 1000)]
+    tickets = {r: gb.gb_submit(*r) for r in order}
+    st_s, rs = gb.gb_poll(tickets[(4, 1000)], -1, check=False)
+    st_b, rb = gb.gb_poll(tickets[(5300, 7400)], -1, check=False)
+    # the failing request fails on its own flags, whichever batch held the
+    # failing tile, and a capped search is not a counterexample
+    assert st_b == gb.GB_ESLOWPATH_LIMIT and rb["status"] == st_b
+    assert rb["counterexample_n"] == 0
+    # the other request is untouched by it
+    assert st_s == 0 and strip(rs) == small_alone
+
+
+def test_capped_slow_path_is_not_a_counterexample(gb):
+    gb.gb_init(2, 5)
+    gb.gb_set_option("slow_cap", 7)
+    for form in ("range", "segments"):
+        if form == "range":
+            r = gb.gb_verify_range(5300, 7400, check=False)
+            recs = []
+        else:
+            recs, r, _ = gb.gb_verify_range_segments(5300, 7400, 64, check=False)
+        assert r["status"] == gb.GB_ESLOWPATH_LIMIT
+        assert r["counterexample_n"] == 0
+        assert all(int(x["counterexample_n"]) == 0 for x in recs)
