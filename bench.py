@@ -204,17 +204,21 @@ def csrc_digest() -> str:
     return h.hexdigest()
 
 
-def measured_traffic(n_count: int):
-    """DRAM bytes per launch of the persistent kernel from the last ncu capture
-    (profiles/persistent_traffic.json), scaled to this launch by even n; None
-    when the kernel sources changed since the capture."""
+def measured_profile(n_count: int):
+    """The last ncu capture of the persistent kernel
+    (profiles/persistent_traffic.json): DRAM bytes (read + write) and executed
+    warp instructions of one launch, for a launch over n_count even n --
+    scaled by n when the capture covered another range, which the result
+    says; None when the kernel sources changed since the capture."""
     try:
         t = json.load(open(os.path.join(ROOT, "profiles", "persistent_traffic.json")))
     except (OSError, ValueError):
         return None
     if t.get("csrc_sha256") != csrc_digest():
         return None
-    return t["dram_bytes"] * n_count / t["n_even"]
+    f = n_count / t["n_even"]
+    return {"traffic": t["dram_bytes"] * f, "inst_executed": t.get("inst_executed", 0) * f or None,
+            "scaled": t["n_even"] != n_count, "captured_n": t["n_even"]}
 
 
 def load_peaks():
@@ -536,7 +540,9 @@ def run_ours(args):
     sm_clock = (peaks or {}).get("sm_max_mhz", 2070.0)
     peak = opt["sms"] * 128 * sm_clock * 1e6          # 4 schedulers x 32 lanes per SM per clock
     achieved = alg["instr"] / (kus * 1e-6) if kus else None
-    traffic = measured_traffic(out["n_count"])
+    prof = measured_profile(out["n_count"])
+    traffic = prof["traffic"] if prof else None
+    executed = prof["inst_executed"] if prof else None
     line = {
         "metric": "even n verified/s at N=1e12", "value": tot_n / (ms * 1e-3),
         "unit": "even_n/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -560,6 +566,13 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": achieved / 1e9 if achieved else None,
                      "peak": peak / 1e9, "unit": "Ginstr/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "traffic_note": (None if not prof else
+                                      f"ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch over "
+                                      f"{prof['captured_n']} even n" + (", scaled to this launch by n"
+                                                                        if prof["scaled"] else "")),
+                     "frac_executed": (executed * 32 / (kus * 1e-6) / peak) if (executed and kus) else None,
+                     "executed_note": "ncu smsp__inst_executed.sum x 32 lanes / (kernel time x issue-slot "
+                                      "peak): the issue slots the kernel filled, useful or not",
                      "kernel": "persistent_kernel", "kernel_us": kus,
                      "algorithmic_instr_per_n": alg["per_n"], "marks_per_n": alg["marks_per_n"],
                      "tail_fraction": alg["tail_fraction"],

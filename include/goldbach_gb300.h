@@ -166,6 +166,10 @@ int gb_init(uint32_t p_max, uint32_t seg_bits);
  *   "timeout_ms"    bound for device-side waits and gb_poll defaults (default 600000)
  *   "tier_b_min"    smallest prime crossed off lane-per-prime (default 16384)
  *   "plain_slice_bits" log2 window bits per CTA in the plain sieve kernel (default 18)
+ *   "plain_search_chunks" search of the plain form: 0 = the per-n search kernel
+ *                   writing a p_min array that a reduce kernel folds (default);
+ *                   4, 6 or 8 = one launch of the bit-parallel search and
+ *                   reduction per segment, reading the global window
  *   "time_kernel"   1 = time the persistent kernel with CUDA events (default 0)
  *   "search_chunks" bit-parallel search over the candidates p < 64 * this: 4, 6 or 8
  *                   (default 4); 0 = one lane per n (wheel 7 allows 0, 4, 8)
@@ -174,12 +178,15 @@ int gb_init(uint32_t p_max, uint32_t seg_bits);
  *                   log2 of the largest n), time the kernel configurations on a
  *                   probe at the top of the range and keep the fastest (tile_bits,
  *                   threads, search_chunks, pattern_max, search_pmax, tier_b_min,
- *                   wheel, builder_warps; combinations with no kernel build are
+ *                   wheel, builder_warps, bucket_min, bucket_chunk_tiles;
+ *                   combinations with no kernel build are
  *                   skipped, and a pipelined one takes the largest tile that
  *                   fits shared memory); the choice is
  *                   cached, and saved to the file named by GB_TUNE_CACHE if set
- *                   (one line per range class: key and the eight values, the
- *                   last builder_warps).
+ *                   (one line per range class: key and ten values, in the
+ *                   order listed here).  A range that needs the bucket
+ *                   pre-pass is probed with it, and bucket_min and
+ *                   bucket_chunk_tiles are tuned too.
  *                   The tuning call synchronises.  Results never depend on it.
  *   "search_pmax"   bound of the in-window candidate search, 0 = P_max (default 0);
  *                   n with p_min above it take the slow path, but n_slow and
@@ -192,9 +199,15 @@ int gb_init(uint32_t p_max, uint32_t seg_bits);
 int gb_set_option(const char *key, int64_t value);
 
 /* gb_get_option -- read back an option, or one of the read-only values
- * "p_max", "seg_bits", "k_words", "sms" and "last_kernel_us" (duration of the
- * last persistent kernel timed with time_kernel = 1, -1 if none; call it
- * after the work has completed).  GB_EINVAL for an unknown key. */
+ * "p_max", "seg_bits", "k_words", "sms", "last_kernel_us" (duration of the
+ * last range kernel timed with time_kernel = 1, -1 if none; for
+ * gb_verify_range_async the events bracket its graph replay, so the clear
+ * and merge launches, a few microseconds, are included; call it after the
+ * work has completed) and "phase_fill", "phase_mark", "phase_search",
+ * "phase_reduce", "phase_warp_bulk", "phase_warp_tail", "phase_claim" (clock64
+ * cycle sums of the last range call, only in the library built with
+ * GB_PHASE_CLOCKS, -1 otherwise; reading one waits for the device).
+ * GB_EINVAL for an unknown key. */
 int gb_get_option(const char *key, int64_t *value);
 
 /* gb_shutdown -- stop the serving thread, let in-flight work finish and free

@@ -16,6 +16,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgoldbach_gb300.so")
+# the same library with per-phase cycle counters in the kernels (GB_PHASE_CLOCKS)
+PHASES_OUT_DIR = os.path.join(HERE, "_build_phases")
+PHASES_LIB = os.path.join(HERE, "libgoldbach_gb300_phases.so")
 SOURCES = ["gb_kernels.cu", "gb_persist_256.cu", "gb_persist_512.cu", "gb_persist_1024.cu", "gb_pipe_8.cu",
            "gb_pipe_16.cu",
            "gb_capi.cu", "gb_serve.cpp", "gb_noalloc.cu", "gb_peaks.cu"]
@@ -29,8 +32,10 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
-def _flags(src: str) -> list[str]:
+def _flags(src: str, phases: bool = False) -> list[str]:
     f = ["-std=c++17", "-O3", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
+    if phases:
+        f.append("-DGB_PHASE_CLOCKS")
     if src.endswith(".cu"):
         f += ARCH + ["-lineinfo", "--expt-relaxed-constexpr"]
     else:
@@ -45,18 +50,21 @@ def _stale(out: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, phases: bool = False) -> str:
+    """Build the library (phases=True: the variant with per-phase cycle
+    counters, a separate file) and return its path."""
+    out_dir, lib = (PHASES_OUT_DIR, PHASES_LIB) if phases else (OUT_DIR, LIB)
+    os.makedirs(out_dir, exist_ok=True)
     headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
     headers.append(os.path.join(ROOT, "include", "goldbach_gb300.h"))
     objs = []
     jobs = []
     for s in SOURCES:
         src = os.path.join(CSRC, s)
-        obj = os.path.join(OUT_DIR, s + ".o")
+        obj = os.path.join(out_dir, s + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + headers + [__file__]):
-            cmd = [nvcc()] + _flags(s) + ["-c", src, "-o", obj]
+            cmd = [nvcc()] + _flags(s, phases) + ["-c", src, "-o", obj]
             jobs.append(cmd)
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         for cmd, res in zip(jobs, ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), jobs)):
@@ -64,15 +72,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
                 sys.stderr.write(" ".join(cmd) + "\n" + res.stdout + res.stderr)
             if res.returncode:
                 raise RuntimeError(f"nvcc failed: {' '.join(cmd)}")
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode:
             sys.stderr.write(" ".join(cmd) + "\n" + res.stdout + res.stderr)
             raise RuntimeError("link failed")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

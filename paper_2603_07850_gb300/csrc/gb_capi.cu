@@ -27,6 +27,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "gb_kernels.h"
 #include "gb_types.h"
@@ -107,6 +108,7 @@ struct Ctx {
     // into the caller's result; each call rewrites the set-params node's
     // arguments in the instantiated graph and replays it on the caller's stream
     cudaGraphExec_t aexec = nullptr;
+    cudaGraph_t agraph = nullptr;          // kept while aexec lives: anode belongs to it
     cudaGraphNode_t anode = nullptr;
     GraphKey akey;
     const void *aout = nullptr;
@@ -129,6 +131,8 @@ struct Ctx {
     uint32_t *d_olist = nullptr;
     size_t olist_cap = 0;
     uint32_t olist_wcap = 0, olist_ctas = 0;
+    // per-phase cycle sums (builds with GB_PHASE_CLOCKS; see Tables::phase)
+    unsigned long long *d_phase = nullptr;
     // balanced order of the tier-A primes (see Tables::aperm) and what it was built for
     uint32_t *d_aperm = nullptr;
     uint32_t aperm_len = 0;
@@ -136,13 +140,24 @@ struct Ctx {
     std::map<uint64_t, uint32_t> odd_primes_below;  // cache: bound -> #odd primes below it
     char dev_name[256] = {0};
     struct TuneCfg {
-        int64_t tile_bits, threads, search_chunks, pattern_max, search_pmax, tier_b_min, wheel, builder_warps;
+        int64_t tile_bits, threads, search_chunks, pattern_max, search_pmax, tier_b_min, wheel, builder_warps,
+            bucket_min, bucket_chunk_tiles;
     };
     std::map<std::string, TuneCfg> tuned;       // autotuner results by range class
     bool ev_pending = false;
 };
 
 Ctx g;
+
+// NVTX range over a host-side phase (table build, tuning, bucket pre-pass,
+// launch or replay, plain segment, serving batch) for a profiler timeline;
+// costs nothing when no tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // The captured graphs bake in table, record and scratch pointers and launch
 // shapes: any change of those makes the next call capture again.
@@ -314,6 +329,7 @@ Tables make_tables(int wheel)
     const bool aperm_fits = g.d_aperm && g.aperm_key[0] == t.iA0 && g.aperm_key[1] == t.iB0;
     t.aperm = aperm_fits ? g.d_aperm : nullptr;
     t.aperm_len = aperm_fits ? g.aperm_len : 0u;
+    t.phase = g.d_phase;
     return t;
 }
 
@@ -359,6 +375,7 @@ int searcher_threads()
 int ensure_table(uint64_t need)
 {
     if (need <= g.table_limit) return GB_OK;
+    NvtxRange nv("gb: base-prime table");
     uint64_t L = std::max<uint64_t>(need, (uint64_t)g.opt.base_limit);
     // round up to 2^k - 1 so repeated growth stays rare
     uint64_t r = 1;
@@ -623,6 +640,7 @@ int enqueue_persistent(cudaStream_t st, const CallPlan &cp, gb_result *dev_out, 
     const int clear_records = g.opt.tile_bits < g.seg_bits ? 1 : 0;
     Tables t = make_tables();
     CK(launch_clear(st, g.d_params, g.d_recs, g.d_ctrl, clear_records, clear_records ? 4 * g.sms : 1));
+    if (g.d_phase) CK(cudaMemsetAsync(g.d_phase, 0, 8ull * PH_COUNT, st));
     if (timed) {
         if (!g.ev0) CK(cudaEventCreate(&g.ev0));
         if (!g.ev1) CK(cudaEventCreate(&g.ev1));
@@ -722,6 +740,7 @@ int run_persistent_buckets(const CallPlan &cp, int grid, size_t smem, int mg, gb
     const int clear_records = g.opt.tile_bits < g.seg_bits ? 1 : 0;
     CK(launch_set_params(st, g.d_params, p));
     CK(launch_clear(st, g.d_params, g.d_recs, g.d_ctrl, clear_records, clear_records ? 4 * g.sms : 1));
+    if (g.d_phase) CK(cudaMemsetAsync(g.d_phase, 0, 8ull * PH_COUNT, st));
     const uint64_t S = 1ull << g.opt.tile_bits, K = 32ull * g.k_words;
     const uint64_t P = isqrt_host(cp.n0 + 2 * (cp.n_total - 1));
     const uint64_t cap = bucket_entries_bound(B, P, g.nprimes - i0, CT * S + K, 1 + (K - 1 + S - 1) / S);
@@ -734,6 +753,7 @@ int run_persistent_buckets(const CallPlan &cp, int grid, size_t smem, int mg, gb
     }
     uint64_t launches = 2;
     for (uint64_t t0 = 0; t0 < cp.ntiles; t0 += CT) {
+        NvtxRange nv("gb: bucket chunk (pre-pass + kernel)");
         const uint32_t nt = (uint32_t)std::min<uint64_t>(CT, cp.ntiles - t0);
         CK(cudaMemsetAsync(g.d_bk_counts, 0, 4ull * nt, st));
         CK(launch_bucket_prepass(st, 4 * g.sms, g.d_params, t, i0, t0, nt, g.d_bk_counts, g.d_bk_off,
@@ -775,7 +795,8 @@ using TuneCfg = Ctx::TuneCfg;
 TuneCfg current_cfg()
 {
     return TuneCfg{g.opt.tile_bits, g.opt.threads, g.opt.search_chunks, g.opt.pattern_max,
-                   g.opt.search_pmax, g.opt.tier_b_min, g.opt.wheel, g.opt.builder_warps};
+                   g.opt.search_pmax, g.opt.tier_b_min, g.opt.wheel, g.opt.builder_warps,
+                   g.opt.bucket_min, g.opt.bucket_chunk_tiles};
 }
 
 int apply_cfg(const TuneCfg &c)
@@ -789,6 +810,8 @@ int apply_cfg(const TuneCfg &c)
     g.opt.tier_b_min = c.tier_b_min;
     g.opt.wheel = c.wheel;
     g.opt.builder_warps = c.builder_warps;
+    g.opt.bucket_min = c.bucket_min;
+    g.opt.bucket_chunk_tiles = c.bucket_chunk_tiles;
     invalidate_graphs();
     return pr ? build_candidates() : GB_OK;
 }
@@ -816,9 +839,25 @@ float time_probe(const CallPlan &probe_in)
     if (!fn || smem > g.smem_optin) return -1.f;
     int grid = 0;
     if (ctx_grid(fn, nt, smem, &grid)) { cudaGetLastError(); return -1.f; }
+    float best = -1.f;
+    if (needs_buckets(probe)) {
+        // the bucket pipeline (pre-pass and kernel per chunk), timed whole
+        if (!g.ev0 && cudaEventCreate(&g.ev0) != cudaSuccess) return -1.f;
+        if (!g.ev1 && cudaEventCreate(&g.ev1) != cudaSuccess) return -1.f;
+        for (int rep = 0; rep < 2; rep++) {
+            if (cudaEventRecord(g.ev0, g.stream) != cudaSuccess) return -1.f;
+            if (run_persistent_buckets(probe, grid, smem, merge_grid_for(probe.nrec), g.d_result, g.stream, false))
+                { cudaGetLastError(); return -1.f; }
+            if (cudaEventRecord(g.ev1, g.stream) != cudaSuccess) return -1.f;
+            if (cudaStreamSynchronize(g.stream) != cudaSuccess) return -1.f;
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, g.ev0, g.ev1) != cudaSuccess) return -1.f;
+            if (best < 0 || ms < best) best = ms;
+        }
+        return best;
+    }
     RangeParams p;
     fill_params(probe, (uint32_t)g.opt.tile_bits, p);
-    float best = -1.f;
     for (int rep = 0; rep < 2; rep++) {
         if (launch_set_params(g.stream, g.d_params, p) != cudaSuccess) return -1.f;
         if (enqueue_persistent(g.stream, probe, g.d_result, grid, smem, merge_grid_for(probe.nrec), true))
@@ -838,9 +877,10 @@ void load_tune_file()
     FILE *f = fopen(path, "r");
     if (!f) return;
     char key[400];
-    long long a, b, c, d, e, h, w, bw;
-    while (fscanf(f, "%399s %lld %lld %lld %lld %lld %lld %lld %lld", key, &a, &b, &c, &d, &e, &h, &w, &bw) == 9)
-        g.tuned[key] = TuneCfg{a, b, c, d, e, h, w, bw};
+    long long a, b, c, d, e, h, w, bw, bm, bt;
+    while (fscanf(f, "%399s %lld %lld %lld %lld %lld %lld %lld %lld %lld %lld", key, &a, &b, &c, &d, &e, &h, &w, &bw,
+                  &bm, &bt) == 11)
+        g.tuned[key] = TuneCfg{a, b, c, d, e, h, w, bw, bm, bt};
     fclose(f);
 }
 
@@ -851,10 +891,11 @@ void save_tune_file()
     FILE *f = fopen(path, "w");
     if (!f) return;
     for (const auto &kv : g.tuned)
-        fprintf(f, "%s %lld %lld %lld %lld %lld %lld %lld %lld\n", kv.first.c_str(), (long long)kv.second.tile_bits,
-                (long long)kv.second.threads, (long long)kv.second.search_chunks,
+        fprintf(f, "%s %lld %lld %lld %lld %lld %lld %lld %lld %lld %lld\n", kv.first.c_str(),
+                (long long)kv.second.tile_bits, (long long)kv.second.threads, (long long)kv.second.search_chunks,
                 (long long)kv.second.pattern_max, (long long)kv.second.search_pmax,
-                (long long)kv.second.tier_b_min, (long long)kv.second.wheel, (long long)kv.second.builder_warps);
+                (long long)kv.second.tier_b_min, (long long)kv.second.wheel, (long long)kv.second.builder_warps,
+                (long long)kv.second.bucket_min, (long long)kv.second.bucket_chunk_tiles);
     fclose(f);
 }
 
@@ -862,7 +903,8 @@ void save_tune_file()
 // the chosen tile size.
 int maybe_autotune(CallPlan &cp)
 {
-    if (!g.opt.autotune || needs_buckets(cp)) return GB_OK;
+    if (!g.opt.autotune) return GB_OK;
+    NvtxRange nv("gb: autotune");
     if (g.tuned.empty()) load_tune_file();
     const std::string key = tune_key(cp);
     auto it = g.tuned.find(key);
@@ -875,7 +917,7 @@ int maybe_autotune(CallPlan &cp)
         if ((rc = ensure_records(probe.nrec))) return rc;
         TuneCfg best = current_cfg();
         float best_ms = time_probe(probe);
-        const std::vector<std::pair<int64_t TuneCfg::*, std::vector<int64_t>>> axes = {
+        std::vector<std::pair<int64_t TuneCfg::*, std::vector<int64_t>>> axes = {
             {&TuneCfg::builder_warps, {0, 8, 12, 16}},       // single-role or pipelined kernel
             {&TuneCfg::search_chunks, {4, 6, 8}},
             {&TuneCfg::tier_b_min, {4096, 16384, 65536}},
@@ -885,6 +927,11 @@ int maybe_autotune(CallPlan &cp)
             {&TuneCfg::pattern_max, {13, 31, 61}},
             {&TuneCfg::search_pmax, {0, 4096, 8192, 16384}},
         };
+        if (needs_buckets(cp)) {
+            // where the bucket pre-pass starts (0 = four window spans) and its chunk size
+            axes.push_back({&TuneCfg::bucket_min, {0, 1 << 21, 1 << 24}});
+            axes.push_back({&TuneCfg::bucket_chunk_tiles, {512, 2048, 8192}});
+        }
         for (int pass = 0; pass < 2; pass++) {
             for (const auto &ax : axes) {
                 for (int64_t v : ax.second) {
@@ -925,6 +972,8 @@ int async_graph(const CallPlan &cp, const RangeParams &p, gb_result *dev_out, in
     key.aperm = tk.aperm; key.aperm_len = tk.aperm_len;
     if (!g.aexec || !(key == g.akey) || g.aout != dev_out) {
         if (g.aexec) { cudaGraphExecDestroy(g.aexec); g.aexec = nullptr; }
+        if (g.agraph) { cudaGraphDestroy(g.agraph); g.agraph = nullptr; }
+        g.anode = nullptr;
         cudaGraph_t graph = nullptr;
         CK(cudaStreamBeginCapture(g.stream, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = launch_set_params(g.stream, g.d_params, p);
@@ -948,11 +997,15 @@ int async_graph(const CallPlan &cp, const RangeParams &p, gb_result *dev_out, in
         }
         if (e == cudaSuccess && !g.anode) e = cudaErrorInvalidValue;
         if (e == cudaSuccess) e = cudaGraphInstantiate(&g.aexec, graph, 0);
-        cudaGraphDestroy(graph);
         if (e != cudaSuccess) {
+            cudaGraphDestroy(graph);
             g.aexec = nullptr;
+            g.anode = nullptr;
             return cuda_status(e, "async graph");
         }
+        // the node handle stays valid only while its graph exists: keep the
+        // graph for later parameter updates of the instantiated copy
+        g.agraph = graph;
         g.akey = key;
         g.aout = dev_out;
         return GB_OK;                                  // captured with this call's params
@@ -1017,7 +1070,10 @@ int run_persistent(uint64_t lo, uint64_t hi, CallPlan &cp)
             CK(e);
             g.gkey = key;
         }
-        CK(cudaGraphLaunch(g.gexec, g.stream));
+        {
+            NvtxRange nv("gb: graph replay");
+            CK(cudaGraphLaunch(g.gexec, g.stream));
+        }
         g.stats.graph_replays++;
     } else {
         CK(cudaMemcpyAsync(g.d_params, g.h_params, sizeof(RangeParams), cudaMemcpyHostToDevice, g.stream));
@@ -1117,6 +1173,7 @@ int run_plain(uint64_t lo, uint64_t hi, CallPlan &cp)
     const uint32_t chunk = (uint32_t)std::min<uint64_t>(1ull << 14, 1ull << g.seg_bits);
     uint64_t launches = 1;
     for (uint64_t s = 0; s < nseg; s++) {
+        NvtxRange nv("gb: plain segment");
         const uint64_t k0 = s << sbits;
         const uint32_t cnt = (uint32_t)std::min<uint64_t>(S, cp.n_total - k0);
         const uint64_t n_lo = cp.n0 + 2 * k0;
@@ -1163,6 +1220,7 @@ void release_all()
     if (g.gexec) { cudaGraphExecDestroy(g.gexec); g.gexec = nullptr; }
     invalidate_graphs();
     if (g.aexec) { cudaGraphExecDestroy(g.aexec); g.aexec = nullptr; }
+    if (g.agraph) { cudaGraphDestroy(g.agraph); g.agraph = nullptr; }
     dev_free(&g.d_primes, 4ull * ((g.nprimes + 3) & ~3ull));
     dev_free(&g.d_recip, 8ull * ((g.nprimes + 3) & ~3ull));
     dev_free(&g.d_PR, 4ull * g.k_words);
@@ -1179,6 +1237,7 @@ void release_all()
     dev_free(&g.d_bk_ent, 4 * g.bk_ent_cap);
     dev_free(&g.d_olist, 4 * g.olist_cap);
     dev_free(&g.d_aperm, 4ull * g.aperm_len);
+    dev_free(&g.d_phase, 8ull * PH_COUNT);
     if (g.h_params) cudaFreeHost(g.h_params);
     if (g.h_result) cudaFreeHost(g.h_result);
     if (g.h_flags) cudaFreeHost(g.h_flags);
@@ -1262,6 +1321,10 @@ int init_locked(uint32_t p_max, uint32_t seg_bits)
     if ((rc = dev_alloc(&g.d_parts, merge_part_bytes() * MERGE_GRID_CAP))) return rc;
     if ((rc = dev_alloc(&g.d_result, sizeof(gb_result)))) return rc;
     CK(cudaMemset(g.d_ctrl, 0, sizeof(Ctrl)));
+#ifdef GB_PHASE_CLOCKS
+    if ((rc = dev_alloc(&g.d_phase, 8ull * PH_COUNT))) return rc;
+    CK(cudaMemset(g.d_phase, 0, 8ull * PH_COUNT));
+#endif
     CK(cudaMallocHost((void **)&g.h_params, sizeof(RangeParams)));
     CK(cudaMallocHost((void **)&g.h_result, sizeof(gb_result)));
     CK(cudaMallocHost((void **)&g.h_flags, 4));
@@ -1542,6 +1605,7 @@ unsigned long long *ctx_serve_items(int buf) { return sv.h_items[buf]; }
 
 int ctx_serve_launch(int buf, size_t n)
 {
+    NvtxRange nv("gb: serving batch launch");
     CK(cudaMemcpyAsync(sv.d_items[buf], sv.h_items[buf], 8ull * n, cudaMemcpyHostToDevice, sv.st));
     CK(cudaMemsetAsync(sv.d_ctrl, 0, sizeof(Ctrl), sv.st));
     Tables t = make_tables(sv.wheel);
@@ -1696,6 +1760,21 @@ int gb_get_option(const char *key, int64_t *value)
         return GB_OK;
     }
     if (!strcmp(key, "seg_bits")) { *value = g.seg_bits; return GB_OK; }
+    // per-phase cycle sums of the last range call (builds with GB_PHASE_CLOCKS;
+    // -1 otherwise); reading one waits for the context's work
+    static const char *phase_keys[PH_COUNT] = {"phase_fill", "phase_mark", "phase_search", "phase_reduce",
+                                               "phase_warp_bulk", "phase_warp_tail", "phase_claim",
+                                               "phase_warp_tier_a", "phase_warp_tier_b"};
+    for (int k = 0; k < PH_COUNT; k++) {
+        if (strcmp(key, phase_keys[k])) continue;
+        *value = -1;
+        if (!g.d_phase) return GB_OK;
+        unsigned long long v[PH_COUNT];
+        CK(cudaDeviceSynchronize());
+        CK(cudaMemcpy(v, g.d_phase, sizeof v, cudaMemcpyDeviceToHost));
+        *value = (int64_t)v[k];
+        return GB_OK;
+    }
     if (!strcmp(key, "sms")) { *value = g.sms; return GB_OK; }
     set_error("unknown option '%s'", key);
     return GB_EINVAL;
@@ -1896,7 +1975,10 @@ int gb_verify_range_async(uint64_t lo, uint64_t hi, gb_result *dev_out, void *st
             if (!g.ev1) CK(cudaEventCreate(&g.ev1));
             CK(cudaEventRecord(g.ev0, st));
         }
-        CK(cudaGraphLaunch(g.aexec, st));
+        {
+            NvtxRange nv("gb: graph replay (async)");
+            CK(cudaGraphLaunch(g.aexec, st));
+        }
         if (timed) {
             CK(cudaEventRecord(g.ev1, st));
             g.ev_pending = true;

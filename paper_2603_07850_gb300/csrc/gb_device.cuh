@@ -18,11 +18,11 @@
 // p*p <= q_hi (p < 2^32 so p*p cannot wrap), and the first multiple is found
 // from wbase mod p as a distance, never by forming a value above q_hi.
 //
-// Per-n p_min search (paper Sec. 3.1 phase 1), the search_chunks = 0 form and
-// the tail of the bit-parallel one (gb_search.cuh): for one n, candidate
-// p = 2i+1 maps to the window bit c - i with c the bit of q = n - 1.  Chunk t
-// is the 32 window bits [c - 32t - 31, c - 32t], one funnel shift of two
-// words, ANDed with the bit-reversed candidate word t; the smallest
+// Per-n p_min search (paper Sec. 3.1 phase 1; gb_search.cuh), the
+// search_chunks = 0 form and the tail of the bit-parallel one: for one n,
+// candidate p = 2i+1 maps to the window bit c - i with c the bit of q = n - 1.
+// Chunk t is the 32 window bits [c - 32t - 31, c - 32t], one funnel shift of
+// two words, ANDed with the bit-reversed candidate word t; the smallest
 // candidate is 32t + clz(mask).
 //
 // Slow path (paper Sec. 3.3, moved onto the GPU): an n with no candidate
@@ -232,6 +232,39 @@ static __device__ __noinline__ unsigned long long slow_pmin(unsigned long long n
         atomicMax(ce_inv, ~n);
     }
     return 0;
+}
+
+// Per-phase cycle counters (builds with GB_PHASE_CLOCKS only; elsewhere no
+// code): the leader thread, just after a barrier, adds the cycles since its
+// previous mark to slot `slot` (slot < 0 only starts the clock).  The last
+// mark lives in one shared word per CTA, so only whole-CTA phases use it.
+__device__ __forceinline__ void phase_mark(const Tables &t, int slot, bool leader)
+{
+#ifdef GB_PHASE_CLOCKS
+    __shared__ unsigned long long s_last;
+    if (leader && t.phase) {
+        const unsigned long long c = clock64();
+        if (slot >= 0) atomicAdd(&t.phase[slot], c - s_last);
+        s_last = c;
+    }
+#else
+    (void)t; (void)slot; (void)leader;
+#endif
+}
+
+// The same for one warp's own phase: cycles since `since` (a clock64 value
+// taken by the warp), added by lane 0; returns the current clock.
+__device__ __forceinline__ unsigned long long phase_warp(const Tables &t, int slot, unsigned long long since)
+{
+#ifdef GB_PHASE_CLOCKS
+    __syncwarp();                                    // the warp's slowest lane ends the phase
+    const unsigned long long c = clock64();
+    if ((threadIdx.x & 31) == 0 && t.phase && slot >= 0) atomicAdd(&t.phase[slot], c - since);
+    return c;
+#else
+    (void)t; (void)slot; (void)since;
+    return 0ull;
+#endif
 }
 
 // Barrier of a group of NTH threads: the whole CTA (BAR = 0, __syncthreads)
@@ -459,6 +492,7 @@ __device__ __forceinline__ void mark_pass(uint32_t *win, const WinGeom &g, const
     // else the ascending primes), 32 at a time: lane q finds the first
     // multiple of the q-th, then the warp marks the 32 primes in turn.
     const uint32_t a_end = t.iB0 < np ? t.iB0 : np;
+    unsigned long long tw = phase_warp(t, -1, 0ull);
     // batch entry e of this warp (lane q holds entry e0 + q NWARP): a prime
     // index, from the balanced order when the host provides one
     const uint32_t e_beg = t.aperm ? 0u : t.iA0, e_end = t.aperm ? t.aperm_len : a_end;
@@ -480,6 +514,7 @@ __device__ __forceinline__ void mark_pass(uint32_t *win, const WinGeom &g, const
                        p, __funnelshift_l(0xfffffffeu, 0xfffffffeu, b));
         }
     }
+    tw = phase_warp(t, PH_WARP_TIER_A, tw);
     // tier B: one lane per prime; the next prime's table entries are loaded
     // while the current one is marked
     const uint32_t iB = (t.iB0 > t.iA0 ? t.iB0 : t.iA0) + threadIdx.x;
@@ -507,6 +542,7 @@ __device__ __forceinline__ void mark_pass(uint32_t *win, const WinGeom &g, const
         }
         for (; j < j_end; j += p) clear_bit(win, j);
     }
+    phase_warp(t, PH_WARP_TIER_B, tw);
 }
 
 // Pass 3: give back the pattern and wheel primes that lie in the window
@@ -557,12 +593,14 @@ __device__ __forceinline__ void build_window(uint32_t *win, const uint32_t *wpat
 {
     fill_pass<WHEEL, NT>(win, wpat, g, t.pat_lo, t.pat_hi, t.groups);
     group_sync<BAR, NT>();
+    phase_mark(t, PH_FILL, BAR == 0 && threadIdx.x == 0);
     uint32_t np = count_le_warp(t.primes, t.nprimes, isqrt_u64(g.q_hi));
     if (np > np_cap) np = np_cap;
     mark_pass<NT>(win, g, t, np);
     if (ent) bucket_pass<NT>(win, g, ent, b0, b1, ctrl);
     fixup_pass<WHEEL>(win, g, t.pat_hi);
     group_sync<BAR, NT>();
+    phase_mark(t, PH_MARK, BAR == 0 && threadIdx.x == 0);
 }
 
 // First odd multiple of p that is >= max(p^2, w), as a distance from w;
@@ -579,33 +617,6 @@ __device__ __forceinline__ unsigned long long first_dist(unsigned long long w, b
     unsigned long long d = r ? (unsigned long long)(p - r) : 0ull;
     if (d & 1ull) d += p;
     return d;
-}
-
-// ---------------------------------------------------------------------------
-// p_min search for one warp chunk of 32 consecutive even n
-// ---------------------------------------------------------------------------
-
-// Lane l handles the n with tile index k = 32 g + l.  win is the window of a
-// tile built by tile_geom (k_words candidate words).  Returns p_min, or 0 if
-// no candidate p <= P_max works (then the caller runs slow_pmin).
-__device__ __forceinline__ uint32_t fast_pmin(const uint32_t *win, const uint32_t *PR,
-                                              uint32_t k_words, uint32_t g, bool active)
-{
-    const uint32_t lane = threadIdx.x & 31;
-    bool done = !active;
-    uint32_t res = 0;
-    const uint32_t wb = g + k_words - 1;
-    for (uint32_t t = 0; t < k_words; ++t) {
-        if (__all_sync(GB_FULL_MASK, done)) break;
-        uint32_t lo = win[wb - t], hi = win[wb - t + 1];
-        uint32_t x = __funnelshift_r(lo, hi, lane);
-        uint32_t m = x & PR[t];
-        if (!done && m) {
-            res = 2u * (32u * t + __clz(m)) + 1u;
-            done = true;
-        }
-    }
-    return res;
 }
 
 }  // namespace gbk

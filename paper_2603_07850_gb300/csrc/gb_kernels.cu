@@ -208,37 +208,51 @@ slice_sieve_kernel(unsigned long long half_abs, int neg, uint32_t j_end, uint32_
 // Entry of the plain form's p_min array for an n whose slow path gave up.
 constexpr uint32_t PM_GAVE_UP = 0xffffffffu;
 
-// p_min for every n of a plain segment, read from the global window bitset.
+// p_min for every n of a plain segment, read from the global window bitset:
+// the per-n search with warp compaction (first chunk of 32 candidates per
+// lane; the n left open finish in full rounds of 32 from candidate 32 on).
 __global__ void __launch_bounds__(256)
 plain_search_kernel(const RangeParams *__restrict__ prm_g, const uint32_t *__restrict__ gwin,
                     const uint32_t *__restrict__ PR, unsigned long long n_lo, uint32_t cnt,
                     uint32_t *__restrict__ pm_out, Ctrl *ctrl)
 {
+    __shared__ uint32_t ring[8][64];
     const RangeParams prm = *prm_g;
-    const int lane = threadIdx.x & 31;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t below = (1u << lane) - 1u;
+    const uint32_t KW = prm.k_words, PR0 = PR[0];
     const uint32_t nchunks = (cnt + 31) >> 5;
-    for (uint32_t g32 = (blockIdx.x * 256u + threadIdx.x) >> 5; g32 < nchunks;
-         g32 += (gridDim.x * 256u) >> 5) {
+    uint32_t *q = ring[warp];
+    uint32_t head = 0, tail = 0;
+    auto finish = [&](uint32_t kk, bool act) {
+        bool gave_up;
+        const uint32_t pm = tail_pmin(gwin, PR, KW, kk, act, n_lo, 32u, prm, ctrl, gave_up);
+        if (act) pm_out[kk] = gave_up ? PM_GAVE_UP : pm;
+    };
+    for (uint32_t g32 = blockIdx.x * 8u + warp; g32 < nchunks; g32 += gridDim.x * 8u) {
         const uint32_t k = (g32 << 5) + lane;
         const bool valid = k < cnt;
         const unsigned long long n = n_lo + 2ull * k;
-        uint32_t pm = fast_pmin(gwin, PR, prm.k_words, g32, valid && n != 4ull);
-        if (valid && n == 4ull) pm = 2u;
-        uint32_t pend = __ballot_sync(GB_FULL_MASK, valid && pm == 0u);
-        while (pend) {
-            const int src = __ffs(pend) - 1;
-            pend &= pend - 1;
-            const unsigned long long ns = __shfl_sync(GB_FULL_MASK, n, src);
-            unsigned long long ps = slow_pmin(ns, prm.p_slow_start, prm.slow_cap_log2, &ctrl->flags, &ctrl->ce_inv);
-            const bool gave_up = ps == SLOW_GAVE_UP;
-            if (!gave_up && ps >= PMIN_LIMIT) {
-                if (lane == 0) atomicOr(&ctrl->flags, F_OVERFLOW);
-                ps = PMIN_LIMIT - 1;
-            }
-            if (lane == src) pm = gave_up ? PM_GAVE_UP : (uint32_t)ps;
+        uint32_t pm = 0;
+        if (valid && n != 4ull) {
+            const uint32_t m = __funnelshift_r(gwin[g32 + KW - 1u], gwin[g32 + KW], lane) & PR0;
+            if (m) pm = 2u * __clz(m) + 1u;
         }
-        if (valid) pm_out[k] = pm;
+        if (pm) pm_out[k] = pm;
+        const bool open = valid && pm == 0u;
+        const uint32_t has = __ballot_sync(GB_FULL_MASK, open);
+        if (open) q[(tail + __popc(has & below)) & 63u] = k;
+        tail += __popc(has);
+        if (tail - head >= 32u) {
+            __syncwarp();
+            const uint32_t kk = q[(head + lane) & 63u];
+            __syncwarp();
+            finish(kk, true);
+            head += 32u;
+        }
     }
+    __syncwarp();
+    if (tail != head) finish(q[(head + lane) & 63u], lane < tail - head);
 }
 
 // Plain form with the bit-parallel search: the CTAs take sub-tiles of 2^(
@@ -370,15 +384,47 @@ table_scatter_kernel(const uint32_t *__restrict__ bits, uint32_t nwords,
     }
 }
 
-__global__ void exclusive_scan_small_kernel(const uint32_t *__restrict__ in, uint32_t n,
-                                            unsigned long long *__restrict__ out)
+// Exclusive scan of n u32 counts into u64 offsets (out[n] = the total), and
+// optionally into u32 cursors, by one 1,024-thread block: each thread sums a
+// run of ceil(n / 1024) counts, the block scans the run sums (warp shuffles,
+// then one warp over the warp totals), and each thread writes its run.  n is
+// at most a few tens of thousands (table blocks, bucket tiles).
+__global__ void __launch_bounds__(1024) block_scan_kernel(const uint32_t *__restrict__ in, uint32_t n,
+                                                          unsigned long long *__restrict__ out,
+                                                          unsigned int *__restrict__ cursor)
 {
-    // one thread: n is at most a few tens of thousands
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        unsigned long long acc = 0;
-        for (uint32_t i = 0; i < n; i++) { out[i] = acc; acc += in[i]; }
-        out[n] = acc;
+    __shared__ unsigned long long s_w[32];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t per = (n + 1023u) / 1024u;
+    const uint32_t b = threadIdx.x * per;
+    const uint32_t e = b + per < n ? b + per : n;
+    unsigned long long sum = 0;
+    for (uint32_t i = b; i < e; i++) sum += in[i];
+    unsigned long long x = sum;                       // inclusive scan over the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(GB_FULL_MASK, x, o);
+        if ((int)lane >= o) x += y;
     }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long v = s_w[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(GB_FULL_MASK, v, o);
+            if ((int)lane >= o) v += y;
+        }
+        s_w[lane] = v;
+    }
+    __syncthreads();
+    unsigned long long acc = x - sum + (warp ? s_w[warp - 1] : 0ull);
+    for (uint32_t i = b; i < e; i++) {
+        out[i] = acc;
+        if (cursor) cursor[i] = (unsigned int)acc;
+        acc += in[i];
+    }
+    if (threadIdx.x == 1023) out[n] = acc;            // an empty run ends at the total too
 }
 
 // ---------------------------------------------------------------------------
@@ -488,20 +534,6 @@ bucket_fill_kernel(const RangeParams *__restrict__ prm_g, Tables t, uint32_t i0,
         });
 }
 
-// Exclusive scan of the bucket counts (one thread; nt is a few thousand).
-__global__ void bucket_scan_kernel(const unsigned int *__restrict__ counts, uint32_t nt,
-                                   unsigned long long *__restrict__ off, unsigned int *__restrict__ cursor)
-{
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    unsigned long long acc = 0;
-    for (uint32_t k = 0; k < nt; k++) {
-        off[k] = acc;
-        cursor[k] = (unsigned int)acc;
-        acc += counts[k];
-    }
-    off[nt] = acc;
-}
-
 __global__ void set_params_kernel(RangeParams *dst, RangeParams p)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) *dst = p;
@@ -519,7 +551,7 @@ cudaError_t launch_bucket_prepass(cudaStream_t st, int grid, const RangeParams *
     const size_t smem = 4ull * nt;
     if (phase == 0) {
         bucket_count_kernel<256><<<grid, 256, smem, st>>>(prm, t, i0, t0, nt, counts);
-        if (cudaPeekAtLastError() == cudaSuccess) bucket_scan_kernel<<<1, 32, 0, st>>>(counts, nt, off, cursor);
+        if (cudaPeekAtLastError() == cudaSuccess) block_scan_kernel<<<1, 1024, 0, st>>>(counts, nt, off, cursor);
     } else {
         bucket_fill_kernel<256><<<grid, 256, smem, st>>>(prm, t, i0, t0, nt, cursor, ent, cap, ctrl);
     }
@@ -684,7 +716,7 @@ cudaError_t launch_table_compact(cudaStream_t st, const uint32_t *bits, uint32_t
     const uint32_t nb = (nwords + TBL_WORDS_PER_BLOCK - 1) / TBL_WORDS_PER_BLOCK;
     if (count_only) {
         table_count_kernel<<<nb, 256, 0, st>>>(bits, nwords, block_counts);
-        exclusive_scan_small_kernel<<<1, 32, 0, st>>>(block_counts, nb, block_offsets);
+        block_scan_kernel<<<1, 1024, 0, st>>>(block_counts, nb, block_offsets, nullptr);
     } else {
         table_scatter_kernel<<<nb, 1024, 0, st>>>(bits, nwords, block_offsets, limit, primes, recip);
     }

@@ -54,7 +54,7 @@ struct LaneAcc {
 // record (plain stores) instead of sharing it (atomics).
 template <int NWARP, int BAR>
 __device__ __forceinline__ void reduce_group(LaneAcc &a, RedScratch &s, DevRec *rec, uint32_t n_cnt, bool whole,
-                                             Ctrl *ctrl, int warp)
+                                             Ctrl *ctrl, int warp, const Tables *tp = nullptr)
 {
     const int lane = threadIdx.x & 31;
     uint32_t wmax = __reduce_max_sync(GB_FULL_MASK, a.mx);
@@ -81,6 +81,7 @@ __device__ __forceinline__ void reduce_group(LaneAcc &a, RedScratch &s, DevRec *
         s.slow[warp] = wslow; s.ce[warp] = wce;
     }
     group_sync<BAR, 32 * NWARP>();
+    if (tp) phase_mark(*tp, PH_SEARCH, BAR == 0 && threadIdx.x == 0);
     if (warp == 0) {
         uint32_t m = lane < NWARP ? s.mx[lane] : 0u;
         unsigned long long ar = lane < NWARP ? s.arg[lane] : ~0ull;
@@ -116,6 +117,7 @@ __device__ __forceinline__ void reduce_group(LaneAcc &a, RedScratch &s, DevRec *
         }
         if (lane == 0 && sl) atomicAdd(&ctrl->slow_total, (unsigned long long)sl);
     }
+    if (tp) phase_mark(*tp, PH_REDUCE, BAR == 0 && threadIdx.x == 0);
 }
 
 // CTA-wide reduction (every thread of an NT-thread CTA).
@@ -171,40 +173,21 @@ __device__ __forceinline__ void search_tile(const RangeParams &prm, unsigned lon
         if (gt < HIST_BINS) s.hist[gt] = 0u;
         if (gt == 0) { s.xslow = 0u; s.xce = 0ull; }
         group_sync<BAR, 32 * NWARP>();
+        SubAcc acc;
+        acc.reset();
+        const SubShared ss{s.hist, &s.xslow, &s.xce};
+        OpenRing rg{&s.ring[warp][0], 0u, 0u};
+        unsigned long long tw = phase_warp(t, -1, 0ull);
         if (SEARCH_BC == 0) {
-            for (uint32_t g32 = (ks >> 5) + warp; (g32 << 5) < ke; g32 += NWARP) {
-                const uint32_t k = (g32 << 5) + lane;
-                const bool valid = k < ke;
-                const unsigned long long n = n_lo + 2ull * k;
-                uint32_t pm = fast_pmin(win, PR, KW, g32, valid && n != 4ull);
-                if (valid && n == 4ull) pm = 2u;
-                uint32_t pend = __ballot_sync(GB_FULL_MASK, valid && pm == 0u);
-                while (pend) {
-                    const int src = __ffs(pend) - 1;
-                    pend &= pend - 1;
-                    const unsigned long long ns = __shfl_sync(GB_FULL_MASK, n, src);
-                    unsigned long long ps = slow_pmin(ns, prm.p_slow_start, prm.slow_cap_log2, &ctrl->flags,
-                                                      &ctrl->ce_inv);
-                    const bool gu = ps == SLOW_GAVE_UP;
-                    if (!gu && ps >= PMIN_LIMIT) {
-                        if (lane == 0) atomicOr(&ctrl->flags, F_OVERFLOW);
-                        ps = PMIN_LIMIT - 1;
-                    }
-                    if (lane == src) {                    // gave up: folded nowhere, the call fails
-                        pm = gu ? 0u : (uint32_t)ps;
-                        if (!gu && !ps) a.ce = a.ce > ~ns ? a.ce : ~ns;
-                    }
-                }
-                if (valid && pm) a.add(pm, kr0 + (k - ks), prm.p_max, s.hist);
-            }
+            // per-n search with warp compaction; the open n finish from candidate 32
+            pern_groups<NWARP>(rg, warp, win, PR, KW, n_lo, ks, ke, prm, acc, ss, ctrl);
+            ring_flush(rg, win, PR, KW, n_lo, ks, 32u, prm, acc, ss, ctrl);
+            tw = phase_warp(t, PH_WARP_TAIL, tw);
         } else {
-            SubAcc acc;
-            acc.reset();
             // this warp's open-mask slots (sized by the host for a whole tile)
             const bool has_list = t.olist && blockIdx.x < t.olist_ctas;
             uint32_t *mb = has_list ? t.olist + ((size_t)blockIdx.x * NWARP + warp) * t.olist_wcap : nullptr;
             const uint32_t gmax = has_list ? t.olist_wcap / 32u : 0u;
-            const SubShared ss{s.hist, &s.xslow, &s.xce};
             const uint32_t one = s.one;                       // 1, a value the compiler cannot see
             const uint32_t wbeg = ks >> 5, wend = (ke + 31) >> 5;
             uint32_t gi = 0;
@@ -227,17 +210,18 @@ __device__ __forceinline__ void search_tile(const RangeParams &prm, unsigned lon
                 gi = gmax;
             }
             __syncwarp();
-            OpenRing rg{&s.ring[warp][0], 0u, 0u};
+            tw = phase_warp(t, PH_WARP_BULK, tw);
             ring_groups<NWARP>(rg, mb, 0u, gi, wbeg + 32u * warp, win, PR, KW, n_lo, ks, i_start, prm, acc, ss, ctrl);
             ring_flush(rg, win, PR, KW, n_lo, ks, i_start, prm, acc, ss, ctrl);
-            a.mx = acc.mx;
-            a.arg = acc.mx ? kr0 + acc.arg : ~0ull;
-            a.sum = acc.sum;
-            a.wsum = acc.wsum + kr0 * acc.sum;
-            a.hA = (unsigned long long)acc.h[0] | ((unsigned long long)acc.h[1] << 32);
-            a.hB = (unsigned long long)acc.h[2] | ((unsigned long long)acc.h[3] << 32);
+            tw = phase_warp(t, PH_WARP_TAIL, tw);
         }
-        reduce_group<NWARP, BAR>(a, s, rec, ke - ks, whole, ctrl, warp);
+        a.mx = acc.mx;
+        a.arg = acc.mx ? kr0 + acc.arg : ~0ull;
+        a.sum = acc.sum;
+        a.wsum = acc.wsum + kr0 * acc.sum;
+        a.hA = (unsigned long long)acc.h[0] | ((unsigned long long)acc.h[1] << 32);
+        a.hB = (unsigned long long)acc.h[2] | ((unsigned long long)acc.h[3] << 32);
+        reduce_group<NWARP, BAR>(a, s, rec, ke - ks, whole, ctrl, warp, &t);
     }
 }
 
@@ -296,10 +280,12 @@ persistent_kernel(const RangeParams *__restrict__ prm_g, Tables t, DevRec *__res
     uint32_t *win = PR + ((KW + 3) & ~3u);
     build_wheel_pattern<WHEEL, NT>(wpat);
     for (uint32_t i = threadIdx.x; i < KW; i += NT) PR[i] = t.PR[i];
+    phase_mark(t, -1, threadIdx.x == 0);
     for (;;) {
         if (threadIdx.x == 0)
             s.tile = prm.tile0 + (prm.claim ? atomicAdd_system(prm.claim, 1ull) : atomicAdd(&ctrl->tile_ctr, 1ull));
         __syncthreads();
+        phase_mark(t, PH_CLAIM, threadIdx.x == 0);
         const unsigned long long tile = s.tile;
         if (tile >= prm.tile_end) break;
         run_tile<WHEEL, NT, SEARCH_BC>(prm, tile, t, wpat, PR, win, s, recs, ctrl);

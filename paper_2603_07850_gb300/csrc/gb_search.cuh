@@ -262,20 +262,22 @@ __device__ __forceinline__ uint32_t bulk_word(const uint32_t *win, uint32_t w, u
     return valid & ~V;
 }
 
-// Per-n search of one open n (tile index k) per lane, from candidate index
-// i_start on, then the exact slow path; folds p_min into acc.  Warp-collective
-// (all 32 lanes call it; `act` marks the lanes that hold an n).
-__device__ __forceinline__ void tail_one(const uint32_t *win, const uint32_t *PR, uint32_t KW, uint32_t k,
-                                         bool act, unsigned long long n_lo, uint32_t ks, uint32_t i_start,
-                                         const RangeParams &prm, SubAcc &acc, const SubShared &ss, Ctrl *ctrl)
+// p_min of one n per lane (tile index k) from candidate index i_start on,
+// then the exact slow path.  Warp-collective (all 32 lanes call it; `act`
+// marks the lanes that hold an n).  Returns p_min, or 0: a counterexample
+// (gave_up false; F_COUNTEREX is set) or a slow path that gave up (gave_up
+// true; the call fails with GB_ESLOWPATH_LIMIT).
+__device__ __forceinline__ uint32_t tail_pmin(const uint32_t *win, const uint32_t *PR, uint32_t KW, uint32_t k,
+                                              bool act, unsigned long long n_lo, uint32_t i_start,
+                                              const RangeParams &prm, Ctrl *ctrl, bool &gave_up)
 {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t KB = 32u * KW;
     const uint32_t t0 = i_start >> 5;
     const uint32_t mask0 = 0xffffffffu >> (i_start & 31u);
-    const uint32_t kr = k - ks;                           // k relative to the sub-record
     const unsigned long long n = n_lo + 2ull * k;
     uint32_t pm = 0;
+    gave_up = false;
     if (act) {
         if (n == 4ull) {
             pm = 2u;
@@ -303,30 +305,50 @@ __device__ __forceinline__ void tail_one(const uint32_t *win, const uint32_t *PR
         pend &= pend - 1;
         const unsigned long long ns = __shfl_sync(GB_FULL_MASK, n, src);
         unsigned long long ps = slow_pmin(ns, prm.p_slow_start, prm.slow_cap_log2, &ctrl->flags, &ctrl->ce_inv);
-        const bool gave_up = ps == SLOW_GAVE_UP;           // the call fails; the n is folded nowhere
-        if (!gave_up && ps >= PMIN_LIMIT) {
+        const bool gu = ps == SLOW_GAVE_UP;
+        if (!gu && ps >= PMIN_LIMIT) {
             if (lane == 0) atomicOr(&ctrl->flags, F_OVERFLOW);
             ps = PMIN_LIMIT - 1;
         }
         if ((int)lane == src) {
-            pm = gave_up ? 0u : (uint32_t)ps;
-            if (!gave_up && !ps) atomicMax(ss.ce, ~ns);
+            pm = gu ? 0u : (uint32_t)ps;
+            gave_up = gu;
         }
     }
-    if (act && pm) {
-        acc.take_max(pm, kr);
-        acc.sum += pm;
-        acc.wsum += (unsigned long long)pm * (kr + 1ull);
-        if (pm > prm.p_max) atomicAdd(ss.slow, 1u);
-        const uint32_t bin = 31u - __clz(pm);
-        if (bin <= 8) {
-            const uint32_t hb = bin - 1u, inc = 1u << (16u * (hb & 1u));
+    return pm;
+}
+
+// Fold one p_min (kr = its index in the sub-record) into the lane's record state.
+__device__ __forceinline__ void fold_pmin(uint32_t pm, uint32_t kr, const RangeParams &prm, SubAcc &acc,
+                                          const SubShared &ss)
+{
+    acc.take_max(pm, kr);
+    acc.sum += pm;
+    acc.wsum += (unsigned long long)pm * (kr + 1ull);
+    if (pm > prm.p_max) atomicAdd(ss.slow, 1u);
+    const uint32_t bin = 31u - __clz(pm);
+    if (bin <= 8) {
+        const uint32_t hb = bin - 1u, inc = 1u << (16u * (hb & 1u));
 #pragma unroll
-            for (uint32_t q = 0; q < 4; q++) acc.h[q] += (hb >> 1) == q ? inc : 0u;
-        } else {
-            atomicAdd(&ss.hist[bin], 1u);
-        }
+        for (uint32_t q = 0; q < 4; q++) acc.h[q] += (hb >> 1) == q ? inc : 0u;
+    } else {
+        atomicAdd(&ss.hist[bin], 1u);
     }
+}
+
+// Per-n search of one open n (tile index k) per lane, from candidate index
+// i_start on, then the exact slow path; folds p_min into acc (a
+// counterexample into the sub-record's shared counter, a slow path that gave
+// up nowhere: the call fails).  Warp-collective (all 32 lanes call it; `act`
+// marks the lanes that hold an n).
+__device__ __forceinline__ void tail_one(const uint32_t *win, const uint32_t *PR, uint32_t KW, uint32_t k,
+                                         bool act, unsigned long long n_lo, uint32_t ks, uint32_t i_start,
+                                         const RangeParams &prm, SubAcc &acc, const SubShared &ss, Ctrl *ctrl)
+{
+    bool gave_up;
+    const uint32_t pm = tail_pmin(win, PR, KW, k, act, n_lo, i_start, prm, ctrl, gave_up);
+    if (act && pm) fold_pmin(pm, k - ks, prm, acc, ss);
+    else if (act && !gave_up) atomicMax(ss.ce, ~(n_lo + 2ull * k));
 }
 
 // The per-n phase of one sub-record for one warp.  During the bulk phase the
@@ -387,6 +409,44 @@ __device__ __forceinline__ void ring_flush(OpenRing &rg, const uint32_t *win, co
     }
     __syncwarp();
     rg.head = rg.tail = 0;
+}
+
+// Per-n search (one lane per n) of the n [ks, ke) of a tile for one warp of
+// NWARP, with warp compaction: each lane looks its n up in the first chunk of
+// 32 candidates (p < 64; one funnel shift of two window words that the whole
+// warp shares); the n left open (and n = 4) go to the warp's ring and finish
+// in full rounds of 32 from candidate 32 on, so no lane idles while another
+// walks far.
+template <int NWARP>
+__device__ __forceinline__ void pern_groups(OpenRing &rg, int warp, const uint32_t *win, const uint32_t *PR,
+                                            uint32_t KW, unsigned long long n_lo, uint32_t ks, uint32_t ke,
+                                            const RangeParams &prm, SubAcc &acc, const SubShared &ss, Ctrl *ctrl)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t below = (1u << lane) - 1u;
+    const uint32_t PR0 = PR[0];
+    for (uint32_t g32 = (ks >> 5) + (uint32_t)warp; (g32 << 5) < ke; g32 += NWARP) {
+        const uint32_t k = (g32 << 5) + lane;
+        const bool valid = k < ke;
+        const unsigned long long n = n_lo + 2ull * k;
+        uint32_t pm = 0;
+        if (valid && n != 4ull) {
+            const uint32_t m = __funnelshift_r(win[g32 + KW - 1u], win[g32 + KW], lane) & PR0;
+            if (m) pm = 2u * __clz(m) + 1u;
+        }
+        if (pm) fold_pmin(pm, k - ks, prm, acc, ss);
+        const bool open = valid && pm == 0u;
+        const uint32_t has = __ballot_sync(GB_FULL_MASK, open);
+        if (open) rg.q[(rg.tail + __popc(has & below)) & 63u] = k;
+        rg.tail += __popc(has);                        // at most 63 entries are pending
+        if (rg.tail - rg.head >= 32u) {
+            __syncwarp();
+            const uint32_t kk = rg.q[(rg.head + lane) & 63u];
+            __syncwarp();
+            tail_one(win, PR, KW, kk, true, n_lo, ks, 32u, prm, acc, ss, ctrl);
+            rg.head += 32u;
+        }
+    }
 }
 
 }  // namespace gbk

@@ -101,6 +101,20 @@ struct Tables {
     // balanced by work; null = round-robin over the ascending primes
     const uint32_t *aperm;
     uint32_t aperm_len;
+    // per-phase clock64 sums of builds with GB_PHASE_CLOCKS defined (slots
+    // PH_*), null otherwise
+    unsigned long long *phase;
+};
+
+// phase slots: CTA cycles (thread 0, between barriers) of the window fill,
+// the crossing-off (marks, buckets, fix-ups), the search and the record
+// reduction; warp cycles (lane 0, summed over warps) of the bit-parallel
+// bulk loop and of the per-n walk of the open n; CTA cycles of the tile
+// claims; warp cycles of the tier-A (warp per prime) and tier-B (lane per
+// prime) crossing-off
+enum : int {
+    PH_FILL = 0, PH_MARK, PH_SEARCH, PH_REDUCE, PH_WARP_BULK, PH_WARP_TAIL, PH_CLAIM, PH_WARP_TIER_A,
+    PH_WARP_TIER_B, PH_COUNT
 };
 
 }  // namespace gbk
