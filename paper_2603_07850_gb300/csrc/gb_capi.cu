@@ -122,7 +122,8 @@ struct Ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // persistent-kernel timing (time_kernel)
     unsigned long long *h_progress = nullptr, *d_progress = nullptr;   // mapped tile counter
     // bucket pre-pass buffers
-    unsigned int *d_bk_counts = nullptr, *d_bk_cursor = nullptr;
+    unsigned int *d_bk_counts = nullptr;
+    unsigned int *d_bk_blk = nullptr;      // per (pre-pass block, tile): count, then first entry
     unsigned long long *d_bk_off = nullptr;
     size_t bk_tiles_cap = 0;
     uint32_t *d_bk_ent = nullptr;
@@ -656,6 +657,9 @@ int enqueue_persistent(cudaStream_t st, const CallPlan &cp, gb_result *dev_out, 
     return GB_OK;
 }
 
+// Blocks of the bucket pre-pass kernels (four per SM).
+size_t bucket_grid() { return 4ull * (size_t)g.sms; }
+
 // Smallest prime handled by the bucket pre-pass for this configuration.
 uint64_t bucket_bound()
 {
@@ -725,11 +729,11 @@ int run_persistent_buckets(const CallPlan &cp, int grid, size_t smem, int mg, gb
     const uint64_t CT = (uint64_t)g.opt.bucket_chunk_tiles;
     if (g.bk_tiles_cap < CT + 1) {
         dev_free(&g.d_bk_counts, 4 * g.bk_tiles_cap);
-        dev_free(&g.d_bk_cursor, 4 * g.bk_tiles_cap);
+        dev_free(&g.d_bk_blk, 4 * g.bk_tiles_cap * bucket_grid());
         dev_free(&g.d_bk_off, 8 * g.bk_tiles_cap);
         g.bk_tiles_cap = 0;
         if ((rc = dev_alloc(&g.d_bk_counts, 4 * (CT + 1)))) return rc;
-        if ((rc = dev_alloc(&g.d_bk_cursor, 4 * (CT + 1)))) return rc;
+        if ((rc = dev_alloc(&g.d_bk_blk, 4 * (CT + 1) * bucket_grid()))) return rc;
         if ((rc = dev_alloc(&g.d_bk_off, 8 * (CT + 1)))) return rc;
         g.bk_tiles_cap = CT + 1;
     }
@@ -756,10 +760,10 @@ int run_persistent_buckets(const CallPlan &cp, int grid, size_t smem, int mg, gb
         NvtxRange nv("gb: bucket chunk (pre-pass + kernel)");
         const uint32_t nt = (uint32_t)std::min<uint64_t>(CT, cp.ntiles - t0);
         CK(cudaMemsetAsync(g.d_bk_counts, 0, 4ull * nt, st));
-        CK(launch_bucket_prepass(st, 4 * g.sms, g.d_params, t, i0, t0, nt, g.d_bk_counts, g.d_bk_off,
-                                 g.d_bk_cursor, nullptr, 0, 0, nullptr));
-        CK(launch_bucket_prepass(st, 4 * g.sms, g.d_params, t, i0, t0, nt, g.d_bk_counts, g.d_bk_off,
-                                 g.d_bk_cursor, g.d_bk_ent, 1, g.bk_ent_cap, g.d_ctrl));
+        CK(launch_bucket_prepass(st, (int)bucket_grid(), g.d_params, t, i0, t0, nt, g.d_bk_counts, g.d_bk_off,
+                                 g.d_bk_blk, nullptr, 0, 0, nullptr));
+        CK(launch_bucket_prepass(st, (int)bucket_grid(), g.d_params, t, i0, t0, nt, g.d_bk_counts, g.d_bk_off,
+                                 g.d_bk_blk, g.d_bk_ent, 1, g.bk_ent_cap, g.d_ctrl));
         p.tile0 = t0;
         p.tile_end = t0 + nt;
         p.bk_off = g.d_bk_off;
@@ -767,7 +771,7 @@ int run_persistent_buckets(const CallPlan &cp, int grid, size_t smem, int mg, gb
         CK(launch_set_params(st, g.d_params, p));
         CK(cudaMemsetAsync(&g.d_ctrl->tile_ctr, 0, 8, st));
         CK(launch_range_kernel(range_kernel(), (int)g.opt.threads, grid, smem, st, g.d_params, t, g.d_recs, g.d_ctrl));
-        launches += 5;
+        launches += 6;
     }
     p.tile0 = 0;
     p.tile_end = cp.ntiles;
@@ -1232,7 +1236,7 @@ void release_all()
     dev_free(&g.d_gwin, 4 * g.gwin_words);
     dev_free(&g.d_pm, 4 * g.pm_cap);
     dev_free(&g.d_bk_counts, 4 * g.bk_tiles_cap);
-    dev_free(&g.d_bk_cursor, 4 * g.bk_tiles_cap);
+    dev_free(&g.d_bk_blk, 4 * g.bk_tiles_cap * bucket_grid());
     dev_free(&g.d_bk_off, 8 * g.bk_tiles_cap);
     dev_free(&g.d_bk_ent, 4 * g.bk_ent_cap);
     dev_free(&g.d_olist, 4 * g.olist_cap);
@@ -1417,7 +1421,7 @@ struct ServeDev {
     // stream-ordered pool, released after the request's last batch
     cudaStream_t pp = nullptr;
     cudaEvent_t ev_prep = nullptr;
-    unsigned int *d_cnt = nullptr, *d_cur = nullptr;
+    unsigned int *d_cnt = nullptr, *d_blk = nullptr;
     unsigned long long *h_total = nullptr;
     std::vector<unsigned long long *> bk_off;
     std::vector<uint32_t *> bk_ent;
@@ -1444,7 +1448,7 @@ int ctx_serve_begin(int max_slots, int max_items)
     CK(cudaStreamCreateWithFlags(&sv.pp, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&sv.ev_prep, cudaEventDisableTiming));
     if ((rc = dev_alloc(&sv.d_cnt, 4ull * (SERVE_BUCKET_MAX_TILES + 1)))) return rc;
-    if ((rc = dev_alloc(&sv.d_cur, 4ull * (SERVE_BUCKET_MAX_TILES + 1)))) return rc;
+    if ((rc = dev_alloc(&sv.d_blk, 4ull * (SERVE_BUCKET_MAX_TILES + 1) * bucket_grid()))) return rc;
     CK(cudaMallocHost((void **)&sv.h_total, 8));
     sv.bk_off.assign(max_slots, nullptr);
     sv.bk_ent.assign(max_slots, nullptr);
@@ -1483,7 +1487,7 @@ void ctx_serve_end()
     }
     cudaStreamSynchronize(sv.st);
     dev_free(&sv.d_cnt, 4ull * (SERVE_BUCKET_MAX_TILES + 1));
-    dev_free(&sv.d_cur, 4ull * (SERVE_BUCKET_MAX_TILES + 1));
+    dev_free(&sv.d_blk, 4ull * (SERVE_BUCKET_MAX_TILES + 1) * bucket_grid());
     if (sv.h_total) cudaFreeHost(sv.h_total);
     if (sv.ev_prep) cudaEventDestroy(sv.ev_prep);
     if (sv.pp) cudaStreamDestroy(sv.pp);
@@ -1570,14 +1574,14 @@ int ctx_serve_init_slot(int slot, const ServePlan &sp, uint64_t *bucket_bytes)
     CK(cudaMemcpyAsync(&sv.d_slots[slot], &h, sizeof h, cudaMemcpyHostToDevice, sv.pp));
     CK(cudaMallocAsync((void **)&off, 8ull * (nt + 1), sv.pp));
     CK(cudaMemsetAsync(sv.d_cnt, 0, 4ull * nt, sv.pp));
-    CK(launch_bucket_prepass(sv.pp, 4 * g.sms, &sv.d_slots[slot].prm, t, h.prm.bk_prime0, 0, nt, sv.d_cnt,
-                             off, sv.d_cur, nullptr, 0, 0, nullptr));
+    CK(launch_bucket_prepass(sv.pp, (int)bucket_grid(), &sv.d_slots[slot].prm, t, h.prm.bk_prime0, 0, nt, sv.d_cnt,
+                             off, sv.d_blk, nullptr, 0, 0, nullptr));
     CK(cudaMemcpyAsync(sv.h_total, off + nt, 8, cudaMemcpyDeviceToHost, sv.pp));
     CK(cudaStreamSynchronize(sv.pp));
     const unsigned long long total = *sv.h_total;
     CK(cudaMallocAsync((void **)&ent, 4ull * total + 16, sv.pp));
-    CK(launch_bucket_prepass(sv.pp, 4 * g.sms, &sv.d_slots[slot].prm, t, h.prm.bk_prime0, 0, nt, sv.d_cnt,
-                             off, sv.d_cur, ent, 1, total, &sv.d_slots[slot].ctl));
+    CK(launch_bucket_prepass(sv.pp, (int)bucket_grid(), &sv.d_slots[slot].prm, t, h.prm.bk_prime0, 0, nt, sv.d_cnt,
+                             off, sv.d_blk, ent, 1, total, &sv.d_slots[slot].ctl));
     h.prm.bk_off = off;
     h.prm.bk_ent = ent;
     CK(cudaMemcpyAsync(&sv.d_slots[slot].prm, &h.prm, sizeof h.prm, cudaMemcpyHostToDevice, sv.pp));

@@ -489,10 +489,13 @@ __device__ __forceinline__ void for_each_hit(const ChunkGeom &c, uint32_t p, uns
     }
 }
 
+// Count the hits of every bucket prime in the windows of tiles [t0, t0 + nt):
+// per block in shared memory, then into counts[k] (all blocks, atomics) and
+// into blk[b nt + k] (block b's own count of tile k, all of them written).
 template <int NT>
 __global__ void __launch_bounds__(NT)
 bucket_count_kernel(const RangeParams *__restrict__ prm_g, Tables t, uint32_t i0, unsigned long long t0,
-                    uint32_t nt, unsigned int *__restrict__ counts)
+                    uint32_t nt, unsigned int *__restrict__ counts, unsigned int *__restrict__ blk)
 {
     extern __shared__ unsigned int h[];
     const RangeParams prm = *prm_g;
@@ -503,33 +506,49 @@ bucket_count_kernel(const RangeParams *__restrict__ prm_g, Tables t, uint32_t i0
     for (uint32_t i = i0 + blockIdx.x * NT + threadIdx.x; i < i1; i += gridDim.x * NT)
         for_each_hit(c, t.primes[i], t.recip[i], [&](uint32_t tt, uint32_t) { atomicAdd(&h[tt], 1u); });
     __syncthreads();
-    for (uint32_t k = threadIdx.x; k < nt; k += NT)
+    unsigned int *mine = blk + (size_t)blockIdx.x * nt;
+    for (uint32_t k = threadIdx.x; k < nt; k += NT) {
+        mine[k] = h[k];
         if (h[k]) atomicAdd(&counts[k], h[k]);
+    }
 }
 
+// Turn the blocks' counts into their first entry in each bucket: tile k's
+// entries start at off[k], block b's at off[k] + the counts of blocks < b.
+__global__ void bucket_block_offsets_kernel(uint32_t nt, uint32_t nblocks, const unsigned long long *__restrict__ off,
+                                            unsigned int *__restrict__ blk)
+{
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nt) return;
+    unsigned int acc = (unsigned int)off[k];         // entries of a chunk stay below 2^32 (host bound)
+    for (uint32_t b = 0; b < nblocks; b++) {
+        const unsigned int c = blk[(size_t)b * nt + k];
+        blk[(size_t)b * nt + k] = acc;
+        acc += c;
+    }
+}
+
+// Write the entries: one more pass over the same primes as the count kernel
+// (same grid, same order), each block appending to its own share of every
+// bucket.  The stores stream (evict-first): the buckets are read once, by
+// the persistent kernel, after the chunk's pre-pass.
 template <int NT>
 __global__ void __launch_bounds__(NT)
 bucket_fill_kernel(const RangeParams *__restrict__ prm_g, Tables t, uint32_t i0, unsigned long long t0,
-                   uint32_t nt, unsigned int *__restrict__ cursor, uint32_t *__restrict__ ent,
+                   uint32_t nt, const unsigned int *__restrict__ blk, uint32_t *__restrict__ ent,
                    unsigned long long cap, Ctrl *ctrl)
 {
     extern __shared__ unsigned int h[];
     const RangeParams prm = *prm_g;
     const ChunkGeom c = chunk_geom(prm, t0, nt);
     const uint32_t i1 = count_le(t.primes, t.nprimes, isqrt_u64(c.q_hi));
-    for (uint32_t k = threadIdx.x; k < nt; k += NT) h[k] = 0u;
-    __syncthreads();
-    for (uint32_t i = i0 + blockIdx.x * NT + threadIdx.x; i < i1; i += gridDim.x * NT)
-        for_each_hit(c, t.primes[i], t.recip[i], [&](uint32_t tt, uint32_t) { atomicAdd(&h[tt], 1u); });
-    __syncthreads();
-    // reserve this block's share of every bucket, then write the entries
-    for (uint32_t k = threadIdx.x; k < nt; k += NT)
-        if (h[k]) h[k] = atomicAdd(&cursor[k], h[k]);
+    const unsigned int *mine = blk + (size_t)blockIdx.x * nt;
+    for (uint32_t k = threadIdx.x; k < nt; k += NT) h[k] = mine[k];
     __syncthreads();
     for (uint32_t i = i0 + blockIdx.x * NT + threadIdx.x; i < i1; i += gridDim.x * NT)
         for_each_hit(c, t.primes[i], t.recip[i], [&](uint32_t tt, uint32_t j) {
             const unsigned int e = atomicAdd(&h[tt], 1u);
-            if (e < cap) ent[e] = j;
+            if (e < cap) __stcs(&ent[e], j);
             else atomicOr(&ctrl->flags, F_INTERNAL);      // the host's capacity bound failed
         });
 }
@@ -545,15 +564,17 @@ __global__ void set_params_kernel(RangeParams *dst, RangeParams p)
 
 cudaError_t launch_bucket_prepass(cudaStream_t st, int grid, const RangeParams *prm, const Tables &t,
                                   uint32_t i0, unsigned long long t0, uint32_t nt, unsigned int *counts,
-                                  unsigned long long *off, unsigned int *cursor, uint32_t *ent, int phase,
+                                  unsigned long long *off, unsigned int *blk, uint32_t *ent, int phase,
                                   unsigned long long cap, Ctrl *ctrl)
 {
     const size_t smem = 4ull * nt;
     if (phase == 0) {
-        bucket_count_kernel<256><<<grid, 256, smem, st>>>(prm, t, i0, t0, nt, counts);
-        if (cudaPeekAtLastError() == cudaSuccess) block_scan_kernel<<<1, 1024, 0, st>>>(counts, nt, off, cursor);
+        bucket_count_kernel<256><<<grid, 256, smem, st>>>(prm, t, i0, t0, nt, counts, blk);
+        if (cudaPeekAtLastError() == cudaSuccess) block_scan_kernel<<<1, 1024, 0, st>>>(counts, nt, off, nullptr);
+        if (cudaPeekAtLastError() == cudaSuccess)
+            bucket_block_offsets_kernel<<<(nt + 255) / 256, 256, 0, st>>>(nt, (uint32_t)grid, off, blk);
     } else {
-        bucket_fill_kernel<256><<<grid, 256, smem, st>>>(prm, t, i0, t0, nt, cursor, ent, cap, ctrl);
+        bucket_fill_kernel<256><<<grid, 256, smem, st>>>(prm, t, i0, t0, nt, blk, ent, cap, ctrl);
     }
     return cudaGetLastError();
 }
