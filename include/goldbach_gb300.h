@@ -147,8 +147,9 @@ int gb_init(uint32_t p_max, uint32_t seg_bits);
  *   "tile_bits"     log2 even n per sieve tile, 10..20 (default 20; at most 19
  *                   with the pipelined kernel and P_max = 2^16, whose CTA
  *                   holds two windows)
- *   "threads"       threads per CTA: 256, 512 or 1024, or 768 with the
- *                   pipelined kernel (default 1024)
+ *   "threads"       threads per CTA: 256, 512, 768 or 1024 (default 1024; the
+ *                   single-role kernel has 768-thread builds for wheel 13 with
+ *                   search_chunks 0, 6 and 8)
  *   "builder_warps" 0 = single-role persistent kernel (every warp builds the
  *                   window, then every warp searches it); 8, 12 or 16 = the
  *                   pipelined kernel, in which that many warps build the next

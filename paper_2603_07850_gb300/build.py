@@ -19,7 +19,8 @@ LIB = os.path.join(HERE, "libgoldbach_gb300.so")
 # the same library with per-phase cycle counters in the kernels (GB_PHASE_CLOCKS)
 PHASES_OUT_DIR = os.path.join(HERE, "_build_phases")
 PHASES_LIB = os.path.join(HERE, "libgoldbach_gb300_phases.so")
-SOURCES = ["gb_kernels.cu", "gb_persist_256.cu", "gb_persist_512.cu", "gb_persist_1024.cu", "gb_pipe_8.cu",
+SOURCES = ["gb_kernels.cu", "gb_persist_256.cu", "gb_persist_512.cu", "gb_persist_768.cu", "gb_persist_1024.cu",
+           "gb_pipe_8.cu",
            "gb_pipe_16.cu",
            "gb_capi.cu", "gb_serve.cpp", "gb_noalloc.cu", "gb_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

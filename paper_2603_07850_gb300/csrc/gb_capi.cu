@@ -625,7 +625,7 @@ int ctx_grid(const void *fn, int nt, size_t smem, int *grid)
 {
     int rc = occupancy_grid(fn, nt, smem, grid);
     if (!rc) rc = ensure_aperm(builder_threads());
-    return rc ? rc : ensure_olist(*grid, searcher_threads(), (uint32_t)g.opt.tile_bits, g.opt.search_chunks != 0);
+    return rc ? rc : ensure_olist(*grid, searcher_threads(), (uint32_t)g.opt.tile_bits, true);
 }
 
 int merge_grid_for(uint64_t nrec)
@@ -925,7 +925,7 @@ int maybe_autotune(CallPlan &cp)
             {&TuneCfg::builder_warps, {0, 8, 12, 16}},       // single-role or pipelined kernel
             {&TuneCfg::search_chunks, {4, 6, 8}},
             {&TuneCfg::tier_b_min, {4096, 16384, 65536}},
-            {&TuneCfg::threads, {256, 512, 1024}},              // 4, 2 or 1 CTAs per SM
+            {&TuneCfg::threads, {256, 512, 768, 1024}},         // 4, 2, 1 or 1 CTAs per SM
             {&TuneCfg::tile_bits, {15, 16, 17, 18, 19, 20, 21}}, // 2^21 never fits shared memory
             {&TuneCfg::wheel, {7, 13}},
             {&TuneCfg::pattern_max, {13, 31, 61}},
@@ -1466,11 +1466,11 @@ int ctx_serve_begin(int max_slots, int max_items)
     sv.wheel = wheel;                               // its tables and pattern block follow it
     sv.smem = persistent_smem((uint32_t)g.opt.tile_bits, wheel);
     if ((rc = occupancy_grid(sv.fn, sv.nt, sv.smem, &sv.grid))) return rc;
-    if (bc != 0) {                                   // the bit-parallel search needs slots
-        sv.olist_wcap = olist_slice(sv.nt);
-        sv.olist_cap = (size_t)sv.grid * (size_t)(sv.nt / 32) * sv.olist_wcap;
-        if ((rc = dev_alloc(&sv.d_olist, 4 * sv.olist_cap))) return rc;
-    }
+    // open-mask slots of the search (both forms use them)
+    sv.olist_wcap = olist_slice(sv.nt);
+    sv.olist_cap = (size_t)sv.grid * (size_t)(sv.nt / 32) * sv.olist_wcap;
+    if ((rc = dev_alloc(&sv.d_olist, 4 * sv.olist_cap))) return rc;
+    (void)bc;
     sv.ready = true;
     return GB_OK;
 }
@@ -1709,7 +1709,7 @@ int gb_set_option(const char *key, int64_t value)
             return GB_EINVAL;
         }
         if (!strcmp(key, "threads") && value != 256 && value != 512 && value != 768 && value != 1024) {
-            set_error("threads must be 256, 512, 768 (pipelined kernel only) or 1024");
+            set_error("threads must be 256, 512, 768 or 1024");
             return GB_EINVAL;
         }
         if (!strcmp(key, "builder_warps") && value != 0 && value != 8 && value != 12 && value != 16) {

@@ -594,6 +594,7 @@ const void *persistent_kernel_ptr(int wheel, int nt, int bc)
 {
     if (nt == 256) return persistent_ptr_256(wheel, bc);
     if (nt == 512) return persistent_ptr_512(wheel, bc);
+    if (nt == 768) return persistent_ptr_768(wheel, bc);
     if (nt == 1024) return persistent_ptr_1024(wheel, bc);
     return nullptr;
 }
@@ -649,16 +650,6 @@ const void *slice_kernel_ptr(int wheel, int nt)
 uint32_t wheel_pattern_words(int wheel)
 {
     return wheel == 13 ? pattern_block_words<13>() : pattern_block_words<7>();
-}
-
-cudaError_t launch_persistent(int wheel, int nt, int bc, int grid, size_t smem, cudaStream_t st,
-                              const RangeParams *prm, const Tables &t, DevRec *recs, Ctrl *ctrl)
-{
-    const void *fn = persistent_kernel_ptr(wheel, nt, bc);
-    if (!fn) return cudaErrorInvalidValue;
-    Tables tt = t;
-    void *args[] = {(void *)&prm, (void *)&tt, (void *)&recs, (void *)&ctrl};
-    return cudaLaunchKernel(fn, dim3(grid), dim3(nt), args, smem, st);
 }
 
 cudaError_t launch_clear(cudaStream_t st, const RangeParams *prm, DevRec *recs, Ctrl *ctrl,

@@ -13,6 +13,9 @@ const void *persistent_kernel_ptr(int wheel, int nt, int bc);
 // defined in gb_persist_<NT>.cu
 const void *persistent_ptr_256(int wheel, int bc);
 const void *persistent_ptr_512(int wheel, int bc);
+const void *persistent_ptr_768(int wheel, int bc);
+// wheel 13, 512 threads, per-n search in one loop: needs no open-mask slots
+const void *persistent_one_loop_ptr_512();
 const void *persistent_ptr_1024(int wheel, int bc);
 const void *serve_ptr_512(int wheel, int bc);
 // pipelined kernel (window-building and searching warps, two window buffers):
@@ -35,8 +38,6 @@ uint32_t wheel_pattern_words(int wheel);
 size_t merge_part_bytes();
 uint32_t table_blocks(uint32_t nwords);
 
-cudaError_t launch_persistent(int wheel, int nt, int bc, int grid, size_t smem, cudaStream_t st,
-                              const RangeParams *prm, const Tables &t, DevRec *recs, Ctrl *ctrl);
 cudaError_t launch_clear(cudaStream_t st, const RangeParams *prm, DevRec *recs, Ctrl *ctrl,
                          int clear_records, int grid);
 cudaError_t launch_merge(cudaStream_t st, int grid, const RangeParams *prm, const DevRec *recs,

@@ -42,8 +42,9 @@ constexpr uint32_t NA_MAX_KWORDS = 1024;          // P_max <= 2^16
 constexpr uint32_t NA_MAX_RECORDS = 8192;
 constexpr uint32_t NA_MERGE_GRID = 512;
 constexpr size_t NA_PART_SLOT = 320;              // >= sizeof(MergePart)
-// the per-n search: the bit-parallel one needs open-mask slots (128 KB per CTA)
-constexpr int NA_TILE_BITS = 20, NA_THREADS = 512, NA_WHEEL = 13, NA_SEARCH_BC = 0;
+// the per-n search in one loop: the other searches need open-mask slots
+// (128 KB per CTA)
+constexpr int NA_TILE_BITS = 20, NA_THREADS = 512, NA_WHEEL = 13;
 
 constexpr size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr size_t OFF_PRIMES = 0;
@@ -287,7 +288,8 @@ extern "C" int gb_verify_range_noalloc(uint64_t lo, uint64_t hi, uint32_t p_max,
     void *d_parts = scr + OFF_PARTS;
     const size_t smem = 4ull * (wheel_pattern_words(NA_WHEEL) + ((k_words + 3) & ~3u) +
                                 ((((1ull << NA_TILE_BITS) + 32ull * k_words) / 32 + 2 + 3) & ~3ull));
-    const void *fn = persistent_kernel_ptr(NA_WHEEL, NA_THREADS, NA_SEARCH_BC);
+    // the per-n search in one loop: the scratch holds no open-mask slots
+    const void *fn = persistent_one_loop_ptr_512();
     int sms = 0, per_sm = 0;
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -303,7 +305,7 @@ extern "C" int gb_verify_range_noalloc(uint64_t lo, uint64_t hi, uint32_t p_max,
     const int clear_records = NA_TILE_BITS < (int)seg_bits ? 1 : 0;
     if (e == cudaSuccess) e = launch_clear(st, d_params, d_recs, d_ctrl, clear_records, clear_records ? 4 * sms : 1);
     if (e == cudaSuccess)
-        e = launch_persistent(NA_WHEEL, NA_THREADS, NA_SEARCH_BC, per_sm * sms, smem, st, d_params, t, d_recs, d_ctrl);
+        e = launch_range_kernel(fn, NA_THREADS, per_sm * sms, smem, st, d_params, t, d_recs, d_ctrl);
     if (e == cudaSuccess) {
         uint64_t mg = (nrec + 255) / 256;
         if (mg > NA_MERGE_GRID) mg = NA_MERGE_GRID;

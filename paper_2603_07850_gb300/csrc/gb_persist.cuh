@@ -144,8 +144,11 @@ __device__ __forceinline__ uint32_t bulk_bound(const RangeParams &prm)
 // Search every n of a tile whose window is built, and reduce it into its
 // record(s).  Run by a group of NWARP warps (the whole CTA, BAR = 0, or the
 // searching warps of the pipelined kernel); `warp` and `gt` are the warp's
-// and the thread's index in the group.
-template <int NWARP, int SEARCH_BC, int BAR>
+// and the thread's index in the group.  ONE_LOOP: the per-n search in one
+// loop, for a launch without open-mask slots (the allocation-free entry
+// point); otherwise both search forms store open masks and finish the open n
+// in a second pass.
+template <int NWARP, int SEARCH_BC, int BAR, bool ONE_LOOP = false>
 __device__ __forceinline__ void search_tile(const RangeParams &prm, unsigned long long tile, const Tables &t,
                                             const uint32_t *PR, const uint32_t *win, RedScratch &s,
                                             DevRec *recs, Ctrl *ctrl, int warp, uint32_t gt)
@@ -178,16 +181,29 @@ __device__ __forceinline__ void search_tile(const RangeParams &prm, unsigned lon
         const SubShared ss{s.hist, &s.xslow, &s.xce};
         OpenRing rg{&s.ring[warp][0], 0u, 0u};
         unsigned long long tw = phase_warp(t, -1, 0ull);
-        if (SEARCH_BC == 0) {
-            // per-n search with warp compaction; the open n finish from candidate 32
+        // this warp's open-mask slots (sized by the host for a whole tile)
+        const bool has_list = t.olist && blockIdx.x < t.olist_ctas;
+        uint32_t *mb = has_list ? t.olist + ((size_t)blockIdx.x * NWARP + warp) * t.olist_wcap : nullptr;
+        const uint32_t gmax = has_list ? t.olist_wcap / 32u : 0u;
+        if (SEARCH_BC == 0 && !ONE_LOOP) {
+            // per-n search: first chunk per lane, then the open n through the
+            // ring from candidate 32, as in the bit-parallel search
+            uint32_t gi = pern_first<NWARP>(win, PR, KW, n_lo, ks, ke, warp, mb, gmax, prm, acc, ss);
+            if (gi > gmax) {                                 // the host sized the slots too small
+                if (lane == 0) atomicOr(&ctrl->flags, F_INTERNAL);
+                gi = gmax;
+            }
+            __syncwarp();
+            tw = phase_warp(t, PH_WARP_BULK, tw);
+            ring_groups<NWARP>(rg, mb, 0u, gi, (ks >> 5) + 32u * warp, win, PR, KW, n_lo, ks, 32u, prm, acc, ss, ctrl);
+            ring_flush(rg, win, PR, KW, n_lo, ks, 32u, prm, acc, ss, ctrl);
+            tw = phase_warp(t, PH_WARP_TAIL, tw);
+        } else if (SEARCH_BC == 0) {
+            // no open-mask slots: the per-n search in one loop
             pern_groups<NWARP>(rg, warp, win, PR, KW, n_lo, ks, ke, prm, acc, ss, ctrl);
             ring_flush(rg, win, PR, KW, n_lo, ks, 32u, prm, acc, ss, ctrl);
             tw = phase_warp(t, PH_WARP_TAIL, tw);
         } else {
-            // this warp's open-mask slots (sized by the host for a whole tile)
-            const bool has_list = t.olist && blockIdx.x < t.olist_ctas;
-            uint32_t *mb = has_list ? t.olist + ((size_t)blockIdx.x * NWARP + warp) * t.olist_wcap : nullptr;
-            const uint32_t gmax = has_list ? t.olist_wcap / 32u : 0u;
             const uint32_t one = s.one;                       // 1, a value the compiler cannot see
             const uint32_t wbeg = ks >> 5, wend = (ke + 31) >> 5;
             uint32_t gi = 0;
@@ -247,13 +263,14 @@ __device__ __forceinline__ void build_tile(const RangeParams &prm, unsigned long
 
 // One tile: build its window, search every n, reduce into its record(s).
 // Called by every thread of the CTA (it contains barriers).
-template <int WHEEL, int NT, int SEARCH_BC>
+template <int WHEEL, int NT, int SEARCH_BC, bool ONE_LOOP = false>
 __device__ __forceinline__ void run_tile(const RangeParams &prm, unsigned long long tile, const Tables &t,
                                          const uint32_t *wpat, const uint32_t *PR, uint32_t *win,
                                          RedScratch &s, DevRec *recs, Ctrl *ctrl)
 {
     build_tile<WHEEL, NT, 0>(prm, tile, t, wpat, win, ctrl);
-    search_tile<NT / 32, SEARCH_BC, 0>(prm, tile, t, PR, win, s, recs, ctrl, (int)(threadIdx.x >> 5), threadIdx.x);
+    search_tile<NT / 32, SEARCH_BC, 0, ONE_LOOP>(prm, tile, t, PR, win, s, recs, ctrl, (int)(threadIdx.x >> 5),
+                                                 threadIdx.x);
 }
 
 // SEARCH_BC = 0: per-n search (one lane per n, 32 candidates per step).
@@ -263,7 +280,7 @@ __device__ __forceinline__ void run_tile(const RangeParams &prm, unsigned long l
 // tiles of at most 2^19 n one CTA can build its window while the other searches.
 template <int NT> constexpr int min_ctas() { return NT == 512 ? 2 : 1; }
 
-template <int WHEEL, int NT, int SEARCH_BC>
+template <int WHEEL, int NT, int SEARCH_BC, bool ONE_LOOP = false>
 __global__ void __launch_bounds__(NT, min_ctas<NT>())
 persistent_kernel(const RangeParams *__restrict__ prm_g, Tables t, DevRec *__restrict__ recs,
                   Ctrl *ctrl)
@@ -288,7 +305,7 @@ persistent_kernel(const RangeParams *__restrict__ prm_g, Tables t, DevRec *__res
         phase_mark(t, PH_CLAIM, threadIdx.x == 0);
         const unsigned long long tile = s.tile;
         if (tile >= prm.tile_end) break;
-        run_tile<WHEEL, NT, SEARCH_BC>(prm, tile, t, wpat, PR, win, s, recs, ctrl);
+        run_tile<WHEEL, NT, SEARCH_BC, ONE_LOOP>(prm, tile, t, wpat, PR, win, s, recs, ctrl);
         if (threadIdx.x == 0 && prm.progress) atomicAdd_system(prm.progress, 1ull);
     }
 }

@@ -23,6 +23,9 @@ const void *persistent_ptr_512(int wheel, int bc)
     return nullptr;
 }
 
+// the per-n search in one loop, for launches without open-mask slots
+const void *persistent_one_loop_ptr_512() { return (const void *)persistent_kernel<13, 512, 0, true>; }
+
 const void *serve_ptr_512(int wheel, int bc)
 {
     if (wheel == 13 && bc == 8) return (const void *)serve_kernel<13, 512, 8>;

@@ -411,8 +411,47 @@ __device__ __forceinline__ void ring_flush(OpenRing &rg, const uint32_t *win, co
     rg.head = rg.tail = 0;
 }
 
+// First pass of the per-n search for one warp of NWARP: the warp takes the
+// same words as the bit-parallel bulk loop (word wg0 + 32 NWARP gi + j, j =
+// 0..31), one word (32 n, one per lane) per step.  Each lane looks its n up
+// in the first chunk of 32 candidates (two window words the whole warp
+// shares), folds the resolved ones, and lane j keeps word j's open mask,
+// stored at mb[32 gi + j] like the bulk loop's; ring_groups then finishes the
+// open n from candidate 32.  Returns the number of word groups.
+template <int NWARP>
+__device__ __forceinline__ uint32_t pern_first(const uint32_t *win, const uint32_t *PR, uint32_t KW,
+                                               unsigned long long n_lo, uint32_t ks, uint32_t ke, int warp,
+                                               uint32_t *mb, uint32_t gmax, const RangeParams &prm, SubAcc &acc,
+                                               const SubShared &ss)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t PR0 = PR[0];
+    const uint32_t wbeg = ks >> 5, wend = (ke + 31) >> 5;
+    uint32_t gi = 0;
+    for (uint32_t wb = wbeg + 32u * (uint32_t)warp; wb < wend; wb += 32u * NWARP, gi++) {
+        uint32_t keep = 0;
+        const uint32_t jn = wend - wb < 32u ? wend - wb : 32u;
+        for (uint32_t j = 0; j < jn; j++) {
+            const uint32_t w = wb + j;
+            const uint32_t k = 32u * w + lane;
+            const bool valid = k < ke;
+            uint32_t pm = 0;
+            if (valid && n_lo + 2ull * k != 4ull) {
+                const uint32_t m = __funnelshift_r(win[w + KW - 1u], win[w + KW], lane) & PR0;
+                if (m) pm = 2u * __clz(m) + 1u;
+            }
+            if (pm) fold_pmin(pm, k - ks, prm, acc, ss);
+            const uint32_t open = __ballot_sync(GB_FULL_MASK, valid && pm == 0u);
+            if (lane == j) keep = open;
+        }
+        if (gi < gmax) mb[32u * gi + lane] = keep;
+    }
+    return gi;
+}
+
 // Per-n search (one lane per n) of the n [ks, ke) of a tile for one warp of
-// NWARP, with warp compaction: each lane looks its n up in the first chunk of
+// NWARP in one loop, for a launch without open-mask slots, with warp
+// compaction: each lane looks its n up in the first chunk of
 // 32 candidates (p < 64; one funnel shift of two window words that the whole
 // warp shares); the n left open (and n = 4) go to the warp's ring and finish
 // in full rounds of 32 from candidate 32 on, so no lane idles while another

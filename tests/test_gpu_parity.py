@@ -102,6 +102,9 @@ def test_small_ranges(gb, lo, hi, seg_bits, tile_bits):
     {"search_pmax": 4096, "search_chunks": 6},
     {"search_pmax": 300, "search_chunks": 6},    # bound inside the bit-parallel range
     {"search_pmax": 40, "search_chunks": 4},     # bound below the second candidate range
+    {"threads": 768, "search_chunks": 6},
+    {"threads": 768, "search_chunks": 0},
+    {"threads": 768, "search_chunks": 8, "tier_b_min": 4096},
 ])
 def test_kernel_options_do_not_change_records(gb, opts):
     check_against_oracle(gb, 4, 2_000_001, 1 << 16, 14, tile_bits=17, **opts)
