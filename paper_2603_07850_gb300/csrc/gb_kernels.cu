@@ -528,30 +528,181 @@ __global__ void bucket_block_offsets_kernel(uint32_t nt, uint32_t nblocks, const
     }
 }
 
-// Write the entries: one more pass over the same primes as the count kernel
-// (same grid, same order), each block appending to its own share of every
-// bucket.  The stores stream (evict-first): the buckets are read once, by
-// the persistent kernel, after the chunk's pre-pass.
+// Block-wide exclusive scan of in[0, n) into out[0, n]; out[n] is the total.
+// Each of the NT threads takes a run of consecutive entries; s_w holds 32
+// words.  Ends with the block's barrier.
 template <int NT>
-__global__ void __launch_bounds__(NT)
-bucket_fill_kernel(const RangeParams *__restrict__ prm_g, Tables t, uint32_t i0, unsigned long long t0,
-                   uint32_t nt, const unsigned int *__restrict__ blk, uint32_t *__restrict__ ent,
-                   unsigned long long cap, Ctrl *ctrl)
+__device__ __forceinline__ void block_exclusive_scan(const uint32_t *in, uint32_t *out, uint32_t n, uint32_t *s_w)
 {
-    extern __shared__ unsigned int h[];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t per = (n + NT - 1) / NT;
+    const uint32_t b = threadIdx.x * per;
+    const uint32_t e = b + per < n ? b + per : n;
+    uint32_t sum = 0;
+    for (uint32_t i = b; i < e; i++) sum += in[i];
+    uint32_t x = sum;                                   // inclusive scan over the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(GB_FULL_MASK, x, o);
+        if ((int)lane >= o) x += y;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t v = lane < NT / 32 ? s_w[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(GB_FULL_MASK, v, o);
+            if ((int)lane >= o) v += y;
+        }
+        s_w[lane] = v;
+    }
+    __syncthreads();
+    uint32_t acc = x - sum + (warp ? s_w[warp - 1] : 0u);
+    for (uint32_t i = b; i < e; i++) {
+        const uint32_t v = in[i];
+        out[i] = acc;
+        acc += v;
+    }
+    if (threadIdx.x == NT - 1) out[n] = acc;            // a thread past n holds the total
+    __syncthreads();
+}
+
+// A thread's position in the enumeration of its primes' entries, in the
+// order of for_each_hit: prime index i is the next prime to take; (tt, j)
+// is the current entry of the hit at distance d of prime p (p = 0: none).
+struct HitCursor {
+    unsigned long long d;
+    uint32_t i, p, tt, j;
+};
+
+__device__ __forceinline__ void cursor_entry(HitCursor &h, const ChunkGeom &c)
+{
+    h.tt = (uint32_t)(h.d >> c.shift);
+    h.j = (uint32_t)((h.d - ((unsigned long long)h.tt << c.shift)) >> 1);
+}
+
+// Move to the first entry of the next prime that hits the chunk; false when
+// the thread's primes are used up.
+__device__ __forceinline__ bool cursor_prime(HitCursor &h, const ChunkGeom &c, const Tables &t, uint32_t i1,
+                                             uint32_t stride)
+{
+    while (h.i < i1) {
+        const uint32_t p = t.primes[h.i];
+        const unsigned long long m = t.recip[h.i];
+        h.i += stride;                                  // i1 < 2^28, stride < 2^20: no wrap
+        const unsigned long long d = first_dist(c.w0, c.neg, c.q_hi, p, m);
+        if (d == ~0ull || d > c.span) continue;
+        h.p = p;
+        h.d = d;
+        cursor_entry(h, c);
+        return true;
+    }
+    h.p = 0;
+    return false;
+}
+
+// Step past the current entry: the same hit in the earlier overlapping
+// window, else the prime's next hit, else the next prime.
+__device__ __forceinline__ bool cursor_next(HitCursor &h, const ChunkGeom &c, const Tables &t, uint32_t i1,
+                                            uint32_t stride)
+{
+    if (h.tt != 0u && h.j + 1u < c.KB) {
+        h.j += c.S;
+        h.tt--;
+        return true;
+    }
+    if (c.span - h.d < 2ull * h.p) return cursor_prime(h, c, t, i1, stride);
+    h.d += 2ull * h.p;
+    cursor_entry(h, c);
+    return true;
+}
+
+// Write the entries, staged in rounds.  Block b takes the primes of the
+// count kernel's blocks FOLD b .. FOLD b + FOLD - 1 (its NT threads are
+// theirs, the grid is theirs / FOLD), so its share of tile k's bucket
+// starts at blk[FOLD b][k].  In each round every thread enumerates its next
+// H entries for this chunk's tiles; the block counts them per tile, ranks
+// them with a scan, enumerates them again into a tile-sorted staging area in
+// shared memory and copies that out, so the entries of one tile leave the
+// block as a run of consecutive slots and the stores coalesce.  The order of
+// the entries inside a bucket is free: each one clears one bit.
+template <int NT, int H, int FOLD>
+__global__ void __launch_bounds__(NT, 1)
+bucket_fill_staged_kernel(const RangeParams *__restrict__ prm_g, Tables t, uint32_t i0, unsigned long long t0,
+                          uint32_t nt, const unsigned int *__restrict__ blk, uint32_t *__restrict__ ent,
+                          unsigned long long cap, Ctrl *ctrl)
+{
+    extern __shared__ uint32_t sm[];
+    uint32_t *pos = sm;                                 // [nt] next slot of this block in tile k's bucket
+    uint32_t *cnt = pos + nt;                           // [nt] entries of tile k in this round
+    uint32_t *base = cnt + nt;                          // [nt + 1] first staging slot of tile k
+    uint32_t *s_w = base + nt + 1;                      // [32] scan scratch
+    uint32_t *sj = s_w + 32;                            // [NT H] staged window bits, by tile
+    uint16_t *stt = (uint16_t *)(sj + NT * H);          // [NT H] their tiles (nt <= 2^16)
     const RangeParams prm = *prm_g;
     const ChunkGeom c = chunk_geom(prm, t0, nt);
     const uint32_t i1 = count_le(t.primes, t.nprimes, isqrt_u64(c.q_hi));
-    const unsigned int *mine = blk + (size_t)blockIdx.x * nt;
-    for (uint32_t k = threadIdx.x; k < nt; k += NT) h[k] = mine[k];
+    const unsigned int *mine = blk + (size_t)blockIdx.x * FOLD * nt;
+    for (uint32_t k = threadIdx.x; k < nt; k += NT) {
+        pos[k] = mine[k];
+        cnt[k] = 0u;
+    }
+    const uint32_t stride = gridDim.x * NT;
+    HitCursor h;
+    h.i = i0 + blockIdx.x * NT + threadIdx.x;
+    h.p = h.tt = h.j = 0u;
+    h.d = 0ull;
+    bool live = cursor_prime(h, c, t, i1, stride);
+    bool over = false;
     __syncthreads();
-    for (uint32_t i = i0 + blockIdx.x * NT + threadIdx.x; i < i1; i += gridDim.x * NT)
-        for_each_hit(c, t.primes[i], t.recip[i], [&](uint32_t tt, uint32_t j) {
-            const unsigned int e = atomicAdd(&h[tt], 1u);
-            if (e < cap) __stcs(&ent[e], j);
-            else atomicOr(&ctrl->flags, F_INTERNAL);      // the host's capacity bound failed
-        });
+    for (;;) {
+        const HitCursor h0 = h;
+        const bool live0 = live;
+        for (int e = 0; live && e < H;) {               // count
+            if (h.tt < nt) {
+                atomicAdd(&cnt[h.tt], 1u);
+                e++;
+            }
+            live = cursor_next(h, c, t, i1, stride);
+        }
+        if (!__syncthreads_or(live0)) break;            // uniform: every thread sees the same
+        block_exclusive_scan<NT>(cnt, base, nt, s_w);
+        for (uint32_t k = threadIdx.x; k < nt; k += NT) cnt[k] = 0u;
+        __syncthreads();
+        HitCursor g = h0;                               // the same entries again, now placed
+        bool l = live0;
+        for (int e = 0; l && e < H;) {
+            if (g.tt < nt) {
+                const uint32_t r = base[g.tt] + atomicAdd(&cnt[g.tt], 1u);
+                sj[r] = g.j;
+                stt[r] = (uint16_t)g.tt;
+                e++;
+            }
+            l = cursor_next(g, c, t, i1, stride);
+        }
+        __syncthreads();
+        const uint32_t total = base[nt];
+        for (uint32_t k = threadIdx.x; k < total; k += NT) {
+            const uint32_t tt = stt[k];
+            const unsigned long long e = (unsigned long long)pos[tt] + (k - base[tt]);
+            if (e < cap) __stcs(&ent[e], sj[k]);
+            else over = true;
+        }
+        __syncthreads();
+        for (uint32_t k = threadIdx.x; k < nt; k += NT) {
+            pos[k] += base[k + 1] - base[k];
+            cnt[k] = 0u;
+        }
+        __syncthreads();
+    }
+    if (over) atomicOr(&ctrl->flags, F_INTERNAL);       // the host's capacity bound failed
 }
+
+constexpr int FILL_NT = 1024, FILL_H = 16, FILL_FOLD = FILL_NT / 256;
+constexpr uint32_t FILL_MAX_TILES = 8192;     // the largest bucket chunk (192 KB of shared memory)
+
+size_t fill_staged_smem(uint32_t nt) { return 4ull * (3ull * nt + 33ull) + 6ull * FILL_NT * FILL_H; }
 
 __global__ void set_params_kernel(RangeParams *dst, RangeParams p)
 {
@@ -574,7 +725,14 @@ cudaError_t launch_bucket_prepass(cudaStream_t st, int grid, const RangeParams *
         if (cudaPeekAtLastError() == cudaSuccess)
             bucket_block_offsets_kernel<<<(nt + 255) / 256, 256, 0, st>>>(nt, (uint32_t)grid, off, blk);
     } else {
-        bucket_fill_kernel<256><<<grid, 256, smem, st>>>(prm, t, i0, t0, nt, blk, ent, cap, ctrl);
+        // the staged fill: FILL_FOLD count blocks to one fill block
+        if (grid % FILL_FOLD != 0 || nt > FILL_MAX_TILES) return cudaErrorInvalidValue;
+        const size_t fs = fill_staged_smem(nt);
+        const cudaError_t e = cudaFuncSetAttribute(bucket_fill_staged_kernel<FILL_NT, FILL_H, FILL_FOLD>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fs);
+        if (e != cudaSuccess) return e;
+        bucket_fill_staged_kernel<FILL_NT, FILL_H, FILL_FOLD><<<grid / FILL_FOLD, FILL_NT, fs, st>>>(
+            prm, t, i0, t0, nt, blk, ent, cap, ctrl);
     }
     return cudaGetLastError();
 }

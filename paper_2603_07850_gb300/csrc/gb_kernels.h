@@ -68,10 +68,12 @@ namespace gbk {
 cudaError_t launch_set_params(cudaStream_t st, RangeParams *dst, const RangeParams &p);
 // the kernel launch_set_params runs (its arguments: RangeParams *dst, RangeParams p)
 const void *set_params_kernel_ptr();
-// phase 0: count hits per tile and per (block, tile), scan the tiles into
-// off, turn blk into each block's first entry per tile; phase 1: fill the
-// entries.  counts holds nt entries (zeroed by the caller), off nt + 1, blk
-// grid * nt; both phases run with the same grid.
+// phase 0: count hits per tile and per (block, tile) with grid blocks of
+// 256 threads, scan the tiles into off, turn blk into each block's first
+// entry per tile; phase 1: fill the entries, staged, with grid / 4 blocks of
+// 1,024 threads (each takes the primes of four count blocks).  counts holds
+// nt entries (zeroed by the caller), off nt + 1, blk grid * nt; grid is a
+// multiple of 4 and nt at most 8,192.
 cudaError_t launch_bucket_prepass(cudaStream_t st, int grid, const RangeParams *prm, const Tables &t,
                                   uint32_t i0, unsigned long long t0, uint32_t nt, unsigned int *counts,
                                   unsigned long long *off, unsigned int *blk, uint32_t *ent, int phase,
