@@ -52,13 +52,16 @@ def main():
                                                        "phase_warp_tier_b")}
     gb.gb_shutdown()
     cta = sum(cyc[k] for k in PHASES)
+    # a range that takes the bucket pre-pass runs several launches and has
+    # no single kernel time: its split is in cycles only
+    ks = kus * 1e-6 if kus > 0 else None
     warp = cyc["phase_warp_bulk"] + cyc["phase_warp_tail"]
     marks = cyc["phase_warp_tier_a"] + cyc["phase_warp_tier_b"]
     print(json.dumps({
-        "range": [args.lo, args.hi], "n_count": r["n_count"], "kernel_s": kus * 1e-6,
+        "range": [args.lo, args.hi], "n_count": r["n_count"], "kernel_s": ks,
         "options": args.option,
         "cta_share": {k[len("phase_"):]: cyc[k] / cta for k in PHASES},
-        "cta_seconds": {k[len("phase_"):]: kus * 1e-6 * cyc[k] / cta for k in PHASES},
+        "cta_seconds": {k[len("phase_"):]: ks * cyc[k] / cta if ks else None for k in PHASES},
         "search_warp_share": {"bulk": cyc["phase_warp_bulk"] / warp if warp else None,
                               "per_n_walk": cyc["phase_warp_tail"] / warp if warp else None},
         "mark_warp_share": {"tier_a": cyc["phase_warp_tier_a"] / marks if marks else None,
