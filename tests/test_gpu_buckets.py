@@ -56,6 +56,18 @@ def test_buckets_match_oracle(gb, bucket_min, chunk, tile_bits, builders):
     assert agg["status"] == 0
 
 
+def test_buckets_largest_chunk(gb):
+    """One chunk of 7,935 tiles: the bucket fill's per-tile arrays at nearly
+    their largest size (chunks of at most 8,192 tiles), and windows that
+    overlap two earlier ones (2^14-n tiles, K = 2^15 bits)."""
+    lo, hi = 10**13 + 2, 10**13 + 2 + 260_000_000
+    recs, agg = run(gb, lo, hi, 1 << 16, 12, tile_bits=14, bucket_min=1 << 15, bucket_chunk_tiles=8192)
+    st, orecs, _, _ = oracle.pmin_range(lo, hi, p_max=1 << 16, seg_bits=12)
+    d = recutil.diff(recs, orecs)
+    assert not d, d
+    assert agg["status"] == 0
+
+
 def _golden_windows():
     g = json.load(open(os.path.join(GOLDEN, "c3_windows.json")))
     out = []
