@@ -195,6 +195,15 @@ int gb_init(uint32_t p_max, uint32_t seg_bits);
  *   "bucket_min"    smallest base prime handled by the bucket pre-pass,
  *                   0 = four window spans, 4 (S + K) (default), else 64 .. 2^28
  *   "bucket_chunk_tiles" tiles per bucket pre-pass chunk, 1..8192 (default 2048)
+ *   "debug_smem_limit" only in the library built with GB_DEBUG
+ *                   (libgoldbach_gb300_debug.so), whose kernels check every
+ *                   access to a sieve window in shared memory: the checks
+ *                   then allow only the first this many bytes of the
+ *                   dynamic shared memory, 0 = all of it (default).  A
+ *                   failed check skips its access and the call fails with
+ *                   GB_EINTERNAL; a lower limit makes checks fail on
+ *                   accesses that are still inside the allocation, to test
+ *                   that path.  Ignored by the ordinary library.
  * Returns GB_OK or GB_EINVAL (unknown key or value out of range).
  */
 int gb_set_option(const char *key, int64_t value);
@@ -207,7 +216,12 @@ int gb_set_option(const char *key, int64_t value);
  * work has completed) and "phase_fill", "phase_mark", "phase_search",
  * "phase_reduce", "phase_warp_bulk", "phase_warp_tail", "phase_claim" (clock64
  * cycle sums of the last range call, only in the library built with
- * GB_PHASE_CLOCKS, -1 otherwise; reading one waits for the device).
+ * GB_PHASE_CLOCKS, -1 otherwise; reading one waits for the device),
+ * "debug_build" (1 in the library built with GB_DEBUG, else 0) and
+ * "debug_bounds_site", "debug_bounds_offset" (that library: the site, 1..8,
+ * and the byte offset in dynamic shared memory of the first failed bounds
+ * check of the last range call, 0 if none; reading one waits for the
+ * device; a serving request's failure shows in its own status only).
  * GB_EINVAL for an unknown key. */
 int gb_get_option(const char *key, int64_t *value);
 

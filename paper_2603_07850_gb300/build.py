@@ -19,6 +19,9 @@ LIB = os.path.join(HERE, "libgoldbach_gb300.so")
 # the same library with per-phase cycle counters in the kernels (GB_PHASE_CLOCKS)
 PHASES_OUT_DIR = os.path.join(HERE, "_build_phases")
 PHASES_LIB = os.path.join(HERE, "libgoldbach_gb300_phases.so")
+# the same library with bounds checks on the shared-memory window (GB_DEBUG)
+DEBUG_OUT_DIR = os.path.join(HERE, "_build_debug")
+DEBUG_LIB = os.path.join(HERE, "libgoldbach_gb300_debug.so")
 SOURCES = ["gb_kernels.cu", "gb_persist_256.cu", "gb_persist_512.cu", "gb_persist_768.cu", "gb_persist_1024.cu",
            "gb_pipe_8.cu",
            "gb_pipe_16.cu",
@@ -33,10 +36,12 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
-def _flags(src: str, phases: bool = False) -> list[str]:
+def _flags(src: str, phases: bool = False, debug: bool = False) -> list[str]:
     f = ["-std=c++17", "-O3", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
     if phases:
         f.append("-DGB_PHASE_CLOCKS")
+    if debug:
+        f.append("-DGB_DEBUG")
     if src.endswith(".cu"):
         f += ARCH + ["-lineinfo", "--expt-relaxed-constexpr"]
     else:
@@ -51,10 +56,14 @@ def _stale(out: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, phases: bool = False) -> str:
-    """Build the library (phases=True: the variant with per-phase cycle
-    counters, a separate file) and return its path."""
-    out_dir, lib = (PHASES_OUT_DIR, PHASES_LIB) if phases else (OUT_DIR, LIB)
+def build(force: bool = False, verbose: bool = False, phases: bool = False, debug: bool = False) -> str:
+    """Build the library and return its path.  phases=True builds the variant
+    with per-phase cycle counters, debug=True the variant with bounds checks
+    on every shared-memory window access; each is a separate file."""
+    if phases and debug:
+        raise ValueError("one variant at a time")
+    out_dir, lib = ((PHASES_OUT_DIR, PHASES_LIB) if phases else (DEBUG_OUT_DIR, DEBUG_LIB) if debug
+                    else (OUT_DIR, LIB))
     os.makedirs(out_dir, exist_ok=True)
     headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
     headers.append(os.path.join(ROOT, "include", "goldbach_gb300.h"))
@@ -65,7 +74,7 @@ def build(force: bool = False, verbose: bool = False, phases: bool = False) -> s
         obj = os.path.join(out_dir, s + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + headers + [__file__]):
-            cmd = [nvcc()] + _flags(s, phases) + ["-c", src, "-o", obj]
+            cmd = [nvcc()] + _flags(s, phases, debug) + ["-c", src, "-o", obj]
             jobs.append(cmd)
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         for cmd, res in zip(jobs, ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), jobs)):

@@ -60,6 +60,8 @@ struct Options {
     int64_t search_chunks = 4;     // bit-parallel search over p < 64 * this (0 = per-n search)
     int64_t autotune = 0;          // 1: tune the kernel configuration per range class
     int64_t builder_warps = 0;     // > 0: pipelined kernel, this many warps build windows
+    int64_t debug_smem_limit = 0;  // builds with GB_DEBUG: bytes of dynamic shared memory the
+                                   // window accesses may touch (0 = the whole allocation)
 };
 
 struct GraphKey {
@@ -373,6 +375,23 @@ int searcher_threads()
 }
 
 // Grow the device base-prime table to every prime <= need (or base_limit).
+// Builds with GB_DEBUG: true, with the error message set, when a kernel's
+// bounds check failed since the control block's debug fields were last
+// cleared; the work must have completed.  Ordinary builds: always false.
+bool debug_bounds_failed(const char *where)
+{
+#ifdef GB_DEBUG
+    Ctrl hc;
+    if (cudaMemcpy(&hc, g.d_ctrl, sizeof hc, cudaMemcpyDeviceToHost) != cudaSuccess || !hc.dbg_site) return false;
+    set_error("bounds check failed while %s: site %u, byte %u of dynamic shared memory", where, hc.dbg_site,
+              hc.dbg_off);
+    return true;
+#else
+    (void)where;
+    return false;
+#endif
+}
+
 int ensure_table(uint64_t need)
 {
     if (need <= g.table_limit) return GB_OK;
@@ -396,9 +415,12 @@ int ensure_table(uint64_t need)
     Tables t = make_tables();                     // still the bootstrap table
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) e = cudaMemsetAsync(bits, 0, 4ull * gwords, g.stream);
+#ifdef GB_DEBUG
+    if (e == cudaSuccess) e = cudaMemsetAsync(&g.d_ctrl->dbg_site, 0, 8, g.stream);   // dbg_site, dbg_off
+#endif
     if (e == cudaSuccess)
         e = launch_slice_sieve((int)g.opt.wheel, nt, (int)((j_end + Z - 1) / Z), smem, g.stream, 0ull, 0,
-                               j_end, Z, t, bits, gwords);
+                               j_end, Z, t, bits, gwords, g.d_ctrl);
     const uint32_t nb = table_blocks(gwords);
     uint32_t *bc = nullptr;
     unsigned long long *bo = nullptr;
@@ -408,10 +430,11 @@ int ensure_table(uint64_t need)
         unsigned long long total = 0;
         if (e == cudaSuccess) e = cudaMemcpyAsync(&total, bo + nb, 8, cudaMemcpyDeviceToHost, g.stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(g.stream);
+        if (e == cudaSuccess && debug_bounds_failed("building the base-prime table")) rc = GB_EINTERNAL;
         uint32_t *np = nullptr;
         unsigned long long *nr = nullptr;
         const uint64_t padded = (total + 3) & ~3ull;       // four-wide loads read up to here
-        if (e == cudaSuccess && (rc = dev_alloc(&np, 4ull * padded)) == GB_OK &&
+        if (e == cudaSuccess && rc == GB_OK && (rc = dev_alloc(&np, 4ull * padded)) == GB_OK &&
             (rc = dev_alloc(&nr, 8ull * padded)) == GB_OK) {
             e = cudaMemsetAsync(np + total, 0, 4ull * (padded - total), g.stream);
             if (e == cudaSuccess) e = cudaMemsetAsync(nr + total, 0, 8ull * (padded - total), g.stream);
@@ -495,6 +518,7 @@ void fill_params(const CallPlan &cp, uint32_t tile_bits, RangeParams &p)
     p.bk_off = nullptr;
     p.bk_ent = nullptr;
     p.progress = g.d_progress;
+    p.dbg_lim = (uint32_t)g.opt.debug_smem_limit;
 }
 
 void empty_result(gb_result *out)
@@ -1187,7 +1211,7 @@ int run_plain(uint64_t lo, uint64_t hi, CallPlan &cp)
         const uint32_t j_end = cnt + kb - 1;
         const int grid = (int)((j_end + Z - 1) / Z);
         CK(launch_slice_sieve((int)g.opt.wheel, nt, grid, smem, g.stream, half_abs, neg ? 1 : 0, j_end, Z,
-                              t, g.d_gwin, (uint32_t)g.gwin_words));
+                              t, g.d_gwin, (uint32_t)g.gwin_words, g.d_ctrl));
         if (pbc) {
             RangeParams ps = *g.h_params;
             ps.tile_bits = sub_bits;
@@ -1372,6 +1396,7 @@ const OptDesc kOpts[] = {
     {"search_chunks", &Options::search_chunks, 0, 8},
     {"autotune", &Options::autotune, 0, 1},
     {"builder_warps", &Options::builder_warps, 0, 16},
+    {"debug_smem_limit", &Options::debug_smem_limit, 0, 1 << 20},
 };
 
 }  // namespace
@@ -1764,6 +1789,29 @@ int gb_get_option(const char *key, int64_t *value)
         return GB_OK;
     }
     if (!strcmp(key, "seg_bits")) { *value = g.seg_bits; return GB_OK; }
+    // bounds checks of the GB_DEBUG build: whether this library has them, and
+    // the site and byte offset of the first failure of the last range call
+    // (0 if none; reading one waits for the context's work)
+    if (!strcmp(key, "debug_build")) {
+#ifdef GB_DEBUG
+        *value = 1;
+#else
+        *value = 0;
+#endif
+        return GB_OK;
+    }
+    if (!strcmp(key, "debug_bounds_site") || !strcmp(key, "debug_bounds_offset")) {
+        *value = 0;
+        if (!g.d_ctrl) return GB_OK;
+        Ctrl hc;
+        if (cudaStreamSynchronize(g.stream) != cudaSuccess ||
+            cudaMemcpy(&hc, g.d_ctrl, sizeof hc, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaGetLastError();
+            return GB_OK;
+        }
+        *value = !strcmp(key, "debug_bounds_site") ? hc.dbg_site : hc.dbg_off;
+        return GB_OK;
+    }
     // per-phase cycle sums of the last range call (builds with GB_PHASE_CLOCKS;
     // -1 otherwise); reading one waits for the context's work
     static const char *phase_keys[PH_COUNT] = {"phase_fill", "phase_mark", "phase_search", "phase_reduce",

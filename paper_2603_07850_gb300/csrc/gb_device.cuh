@@ -39,6 +39,102 @@ namespace gbk {
 
 #define GB_FULL_MASK 0xffffffffu
 
+// ---------------------------------------------------------------------------
+// bounds-checked window accesses (GB_DEBUG builds)
+// ---------------------------------------------------------------------------
+//
+// Every read, store and atomic on a sieve window goes through wld / wst /
+// wand / wor.  In an ordinary build they are the plain access.  In a build
+// with GB_DEBUG an access to shared memory is first checked against the
+// CTA's dynamic shared memory (or its first RangeParams::dbg_lim bytes): one
+// outside is skipped (a load reads 0), and the first failing site and its
+// byte offset are kept in shared memory.  The kernel's epilogue (dbg_end, or
+// dbg_report per serving tile) moves them to the control block with
+// F_BOUNDS | F_INTERNAL, so the call fails with GB_EINTERNAL instead of the
+// access faulting.  dbg_check does the same for a logical index bound.
+// Accesses to global memory are not checked.
+enum DbgSite : uint32_t {
+    DS_FILL = 1, DS_MARK_A = 2, DS_MARK_BIT = 3, DS_FIXUP = 4, DS_BULK = 5, DS_TAIL = 6, DS_PERN = 7,
+    DS_STAGE = 8
+};
+
+#ifdef GB_DEBUG
+extern __shared__ __align__(16) uint32_t gb_dyn_smem[];
+static __shared__ uint32_t gb_dbg_site, gb_dbg_off, gb_dbg_lim;
+
+__device__ __forceinline__ void dbg_fail(uint32_t site, uint32_t off)
+{
+    if (atomicCAS(&gb_dbg_site, 0u, site) == 0u) gb_dbg_off = off;
+}
+
+__device__ __forceinline__ bool dbg_ok(const void *p, uint32_t site)
+{
+    if (!__isShared(p)) return true;
+    uint32_t size;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(size));
+    const uint32_t base = (uint32_t)__cvta_generic_to_shared(gb_dyn_smem);
+    const uint32_t off = (uint32_t)__cvta_generic_to_shared(p);
+    const uint32_t lim = gb_dbg_lim && gb_dbg_lim < size ? gb_dbg_lim : size;
+    if (off >= base && off - base + 4u <= lim) return true;
+    dbg_fail(site, off - base);
+    return false;
+}
+
+__device__ __forceinline__ bool dbg_check(bool in, uint32_t site, uint32_t value)
+{
+    if (!in) dbg_fail(site, value);
+    return in;
+}
+
+// Before the kernel's first barrier, by every thread (thread 0 writes).
+__device__ __forceinline__ void dbg_begin(uint32_t lim)
+{
+    if (threadIdx.x == 0) {
+        gb_dbg_site = 0u;
+        gb_dbg_off = 0u;
+        gb_dbg_lim = lim;
+    }
+}
+
+// Thread 0, with every other thread of the CTA past its last window access:
+// move a failure into ctrl and clear it.
+__device__ __forceinline__ void dbg_report(Ctrl *ctrl)
+{
+    const uint32_t site = atomicExch(&gb_dbg_site, 0u);
+    if (site && ctrl) {
+        if (atomicCAS(&ctrl->dbg_site, 0u, site) == 0u) ctrl->dbg_off = gb_dbg_off;
+        atomicOr(&ctrl->flags, F_BOUNDS | F_INTERNAL);
+    }
+}
+
+// At the end of the kernel, by every thread of the CTA.
+__device__ __forceinline__ void dbg_end(Ctrl *ctrl)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) dbg_report(ctrl);
+}
+#else
+__device__ __forceinline__ bool dbg_ok(const void *, uint32_t) { return true; }
+__device__ __forceinline__ bool dbg_check(bool, uint32_t, uint32_t) { return true; }
+__device__ __forceinline__ void dbg_begin(uint32_t) {}
+__device__ __forceinline__ void dbg_report(Ctrl *) {}
+__device__ __forceinline__ void dbg_end(Ctrl *) {}
+#endif
+
+__device__ __forceinline__ uint32_t wld(const uint32_t *p, uint32_t site) { return dbg_ok(p, site) ? *p : 0u; }
+__device__ __forceinline__ void wst(uint32_t *p, uint32_t v, uint32_t site)
+{
+    if (dbg_ok(p, site)) *p = v;
+}
+__device__ __forceinline__ void wand(uint32_t *p, uint32_t m, uint32_t site)
+{
+    if (dbg_ok(p, site)) atomicAnd(p, m);
+}
+__device__ __forceinline__ void wor(uint32_t *p, uint32_t m, uint32_t site)
+{
+    if (dbg_ok(p, site)) atomicOr(p, m);
+}
+
 // Primes cleared by in-register masks during the fill (those above the wheel).
 // A constexpr function so that, in unrolled loops, every p is a compile-time
 // constant and every "mod p" becomes a multiply-high.
@@ -421,7 +517,7 @@ __device__ __forceinline__ void fill_words(uint32_t *win, const uint32_t *wpat, 
         uint32_t jw = 32u * w;
         if (jw + 32 > g.j_end) word &= (g.j_end > jw) ? (0xffffffffu >> (32 - (g.j_end - jw))) : 0u;
         if (g.clear_upto > jw) word &= (g.clear_upto >= jw + 32) ? 0u : (0xffffffffu << (g.clear_upto - jw));
-        win[w] = word;
+        wst(&win[w], word, DS_FILL);
         u += STEP_M;
         if (u >= M) u -= M;
         if (use1) { u1 += STEP_1; if (u1 >= G1_M) u1 -= G1_M; }
@@ -463,18 +559,18 @@ __device__ __forceinline__ uint32_t first_bit(const WinGeom &g, uint32_t p, unsi
 __device__ __forceinline__ void mark_words(uint32_t *win, uint32_t w, uint32_t w_end, uint32_t p, uint32_t m)
 {
     for (; w + 3u * p < w_end; w += 4u * p) {
-        atomicAnd(&win[w], m);
-        atomicAnd(&win[w + p], m);
-        atomicAnd(&win[w + 2u * p], m);
-        atomicAnd(&win[w + 3u * p], m);
+        wand(&win[w], m, DS_MARK_A);
+        wand(&win[w + p], m, DS_MARK_A);
+        wand(&win[w + 2u * p], m, DS_MARK_A);
+        wand(&win[w + 3u * p], m, DS_MARK_A);
     }
-    for (; w < w_end; w += p) atomicAnd(&win[w], m);
+    for (; w < w_end; w += p) wand(&win[w], m, DS_MARK_A);
 }
 
 __device__ __forceinline__ void clear_bit(uint32_t *win, uint32_t j)
 {
     // ~(1 << (j mod 32)) as one rotate: a funnel shift of 0xfffffffe with itself
-    atomicAnd(&win[j >> 5], __funnelshift_l(0xfffffffeu, 0xfffffffeu, j));
+    wand(&win[j >> 5], __funnelshift_l(0xfffffffeu, 0xfffffffeu, j), DS_MARK_BIT);
 }
 
 // Pass 2: cross off the odd multiples of primes[iA0 .. np) in the window.
@@ -563,7 +659,7 @@ __device__ __forceinline__ void fixup_pass(uint32_t *win, const WinGeom &g, uint
         const bool inside = g.neg ? true : (q >= g.wbase);
         if (!inside || q > g.q_hi) continue;
         const unsigned long long j = d >> 1;
-        if (j < g.j_end) atomicOr(&win[j >> 5], 1u << (j & 31));
+        if (j < g.j_end) wor(&win[j >> 5], 1u << (j & 31), DS_FIXUP);
     }
 }
 

@@ -31,6 +31,7 @@ __global__ void clear_kernel(const RangeParams *__restrict__ prm_g, DevRec *recs
     if (tid == 0) {
         ctrl->tile_ctr = 0; ctrl->ce_inv = 0; ctrl->slow_total = 0; ctrl->flags = 0;
         ctrl->merge_done = 0; ctrl->work_ctr = 0;
+        ctrl->dbg_site = 0; ctrl->dbg_off = 0;
     }
     if (!clear_records) return;
     const unsigned long long words = prm.nrec * (sizeof(DevRec) / 16);
@@ -182,12 +183,13 @@ __device__ __forceinline__ WinGeom slice_geom(unsigned long long half_abs, bool 
 template <int WHEEL, int NT>
 __global__ void __launch_bounds__(NT, 1)
 slice_sieve_kernel(unsigned long long half_abs, int neg, uint32_t j_end, uint32_t Z, Tables t,
-                   uint32_t *__restrict__ gwin, uint32_t gwords)
+                   uint32_t *__restrict__ gwin, uint32_t gwords, Ctrl *ctrl)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     constexpr uint32_t WP = pattern_block_words<WHEEL>();
     uint32_t *wpat = smem;
     uint32_t *win = smem + WP;
+    dbg_begin(0u);
     build_wheel_pattern<WHEEL, NT>(wpat);
     __syncthreads();
     const uint32_t z0 = blockIdx.x * Z;
@@ -203,6 +205,7 @@ slice_sieve_kernel(unsigned long long half_abs, int neg, uint32_t j_end, uint32_
     const uint4 *src = reinterpret_cast<const uint4 *>(win);
     for (uint32_t i = threadIdx.x; i < n4; i += NT) dst[i] = src[i];
     for (uint32_t i = 4 * n4 + threadIdx.x; i < nw; i += NT) gwin[w0 + i] = win[i];
+    dbg_end(ctrl);
 }
 
 // Entry of the plain form's p_min array for an n whose slow path gave up.
@@ -267,6 +270,7 @@ plain_bulk_kernel(RangeParams prm, unsigned long long tile_first, uint32_t nsub,
 {
     extern __shared__ __align__(16) uint32_t PRs[];
     __shared__ RedScratch s;
+    dbg_begin(prm.dbg_lim);
     for (uint32_t i = threadIdx.x; i < prm.k_words; i += NT) PRs[i] = t.PR[i];
     if (threadIdx.x == 0) s.one = 1u;
     __syncthreads();
@@ -275,6 +279,7 @@ plain_bulk_kernel(RangeParams prm, unsigned long long tile_first, uint32_t nsub,
                                     ctrl, (int)(threadIdx.x >> 5), threadIdx.x);
         __syncthreads();
     }
+    dbg_end(ctrl);
 }
 
 // Reduce chunks of the p_min array into (zeroed) records with atomics.
@@ -644,6 +649,7 @@ bucket_fill_staged_kernel(const RangeParams *__restrict__ prm_g, Tables t, uint3
     const ChunkGeom c = chunk_geom(prm, t0, nt);
     const uint32_t i1 = count_le(t.primes, t.nprimes, isqrt_u64(c.q_hi));
     const unsigned int *mine = blk + (size_t)blockIdx.x * FOLD * nt;
+    dbg_begin(0u);
     for (uint32_t k = threadIdx.x; k < nt; k += NT) {
         pos[k] = mine[k];
         cnt[k] = 0u;
@@ -675,8 +681,10 @@ bucket_fill_staged_kernel(const RangeParams *__restrict__ prm_g, Tables t, uint3
         for (int e = 0; l && e < H;) {
             if (g.tt < nt) {
                 const uint32_t r = base[g.tt] + atomicAdd(&cnt[g.tt], 1u);
-                sj[r] = g.j;
-                stt[r] = (uint16_t)g.tt;
+                if (dbg_check(r < NT * H, DS_STAGE, r)) {
+                    sj[r] = g.j;
+                    stt[r] = (uint16_t)g.tt;
+                }
                 e++;
             }
             l = cursor_next(g, c, t, i1, stride);
@@ -697,6 +705,7 @@ bucket_fill_staged_kernel(const RangeParams *__restrict__ prm_g, Tables t, uint3
         __syncthreads();
     }
     if (over) atomicOr(&ctrl->flags, F_INTERNAL);       // the host's capacity bound failed
+    dbg_end(ctrl);
 }
 
 constexpr int FILL_NT = 1024, FILL_H = 16, FILL_FOLD = FILL_NT / 256;
@@ -851,13 +860,13 @@ cudaError_t launch_plain_bulk(int bc, int grid, size_t smem, cudaStream_t st, co
 
 cudaError_t launch_slice_sieve(int wheel, int nt, int grid, size_t smem, cudaStream_t st,
                                unsigned long long half_abs, int neg, uint32_t j_end, uint32_t Z,
-                               const Tables &t, uint32_t *gwin, uint32_t gwords)
+                               const Tables &t, uint32_t *gwin, uint32_t gwords, Ctrl *ctrl)
 {
     const void *fn = slice_kernel_ptr(wheel, nt);
     if (!fn) return cudaErrorInvalidValue;
     Tables tt = t;
     void *args[] = {(void *)&half_abs, (void *)&neg, (void *)&j_end, (void *)&Z, (void *)&tt,
-                    (void *)&gwin, (void *)&gwords};
+                    (void *)&gwin, (void *)&gwords, (void *)&ctrl};
     return cudaLaunchKernel(fn, dim3(grid), dim3(nt), args, smem, st);
 }
 

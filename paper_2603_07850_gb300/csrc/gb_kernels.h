@@ -44,7 +44,7 @@ cudaError_t launch_merge(cudaStream_t st, int grid, const RangeParams *prm, cons
                          Ctrl *ctrl, void *parts, gb_result *out);
 cudaError_t launch_slice_sieve(int wheel, int nt, int grid, size_t smem, cudaStream_t st,
                                unsigned long long half_abs, int neg, uint32_t j_end, uint32_t Z,
-                               const Tables &t, uint32_t *gwin, uint32_t gwords);
+                               const Tables &t, uint32_t *gwin, uint32_t gwords, Ctrl *ctrl);
 cudaError_t launch_plain_search(cudaStream_t st, int grid, const RangeParams *prm,
                                 const uint32_t *gwin, const uint32_t *PR, unsigned long long n_lo,
                                 uint32_t cnt, uint32_t *pm, Ctrl *ctrl);

@@ -288,6 +288,7 @@ persistent_kernel(const RangeParams *__restrict__ prm_g, Tables t, DevRec *__res
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ RedScratch s;
     constexpr uint32_t WP = pattern_block_words<WHEEL>();
+    dbg_begin(prm_g->dbg_lim);
     // the call's parameters live in shared memory, not in registers
     if (threadIdx.x == 0) { s.prm = *prm_g; s.one = 1u; }
     const RangeParams &prm = s.prm;
@@ -308,6 +309,7 @@ persistent_kernel(const RangeParams *__restrict__ prm_g, Tables t, DevRec *__res
         run_tile<WHEEL, NT, SEARCH_BC, ONE_LOOP>(prm, tile, t, wpat, PR, win, s, recs, ctrl);
         if (threadIdx.x == 0 && prm.progress) atomicAdd_system(prm.progress, 1ull);
     }
+    dbg_end(ctrl);
 }
 
 // ---------------------------------------------------------------------------
@@ -335,6 +337,7 @@ pipe_kernel(const RangeParams *__restrict__ prm_g, Tables t, DevRec *__restrict_
     __shared__ RedScratch s;
     __shared__ unsigned long long s_tile[2];
     constexpr uint32_t WP = pattern_block_words<WHEEL>();
+    dbg_begin(prm_g->dbg_lim);
     if (threadIdx.x == 0) { s.prm = *prm_g; s.one = 1u; }
     const RangeParams &prm = s.prm;
     const uint32_t KW = prm_g->k_words;
@@ -372,6 +375,7 @@ pipe_kernel(const RangeParams *__restrict__ prm_g, Tables t, DevRec *__restrict_
         }
         __syncthreads();
     }
+    dbg_end(ctrl);
     (void)NCT;
 }
 
@@ -391,12 +395,15 @@ serve_kernel(const unsigned long long *__restrict__ items, unsigned long long n_
     uint32_t *wpat = smem;
     uint32_t *PR = wpat + WP;
     uint32_t *win = PR + ((KW + 3) & ~3u);
+    dbg_begin(0u);
     build_wheel_pattern<WHEEL, NT>(wpat);
     for (uint32_t i = threadIdx.x; i < KW; i += NT) PR[i] = t.PR[i];
     if (threadIdx.x == 0) s.one = 1u;
+    Ctrl *last_ctl = nullptr;                    // thread 0: the request of the CTA's last tile
     for (;;) {
         __syncthreads();                         // every thread is done with the last tile's params
         if (threadIdx.x == 0) {
+            dbg_report(last_ctl);                // a failed bounds check of that tile fails its request
             const unsigned long long i = atomicAdd(&ctrl->work_ctr, 1ull);
             s.tile = i;
             if (i < n_items) s.prm = slots[items[i] >> SERVE_SLOT_SHIFT].prm;
@@ -407,6 +414,7 @@ serve_kernel(const unsigned long long *__restrict__ items, unsigned long long n_
         const unsigned long long item = items[idx];
         const unsigned long long slot = item >> SERVE_SLOT_SHIFT;
         const unsigned long long tile = item & ((1ull << SERVE_SLOT_SHIFT) - 1ull);
+        if (threadIdx.x == 0) last_ctl = &slots[slot].ctl;
         run_tile<WHEEL, NT, SEARCH_BC>(s.prm, tile, t, wpat, PR, win, s, &slots[slot].acc, &slots[slot].ctl);
     }
 }

@@ -201,7 +201,8 @@ __device__ __forceinline__ uint32_t bulk_word(const uint32_t *win, uint32_t w, u
         // possible when !ALL, with a search bound below 64 BC): it loads
         // nothing, so no index runs below the window
         const bool cin = ALL || (uint32_t)c < KW;
-        const uint32_t lo = cin ? win[w + KW - 1 - c] : 0u, hi = cin ? win[w + KW - c] : 0u;
+        const uint32_t lo = cin ? wld(&win[w + KW - 1 - c], DS_BULK) : 0u,
+                       hi = cin ? wld(&win[w + KW - c], DS_BULK) : 0u;
 #pragma unroll
         for (int h = 0; h < 2; h++) {
             const uint32_t g = 2u * c + h;                // p in [32 g, 32 g + 32)
@@ -287,13 +288,13 @@ __device__ __forceinline__ uint32_t tail_pmin(const uint32_t *win, const uint32_
             // chunk t's low word, so each step loads one window word
             const uint32_t s0 = k + KB - 32u - 32u * t0;
             const uint32_t sh = s0 & 31u;
-            uint32_t w = s0 >> 5, hi = win[w + 1];
-            uint32_t lo = win[w];
+            uint32_t w = s0 >> 5, hi = wld(&win[w + 1], DS_TAIL);
+            uint32_t lo = wld(&win[w], DS_TAIL);
             uint32_t m = __funnelshift_r(lo, hi, sh) & PR[t0] & mask0;
             uint32_t t = t0;
             while (!m && ++t < KW) {
                 hi = lo;
-                lo = win[--w];
+                lo = wld(&win[--w], DS_TAIL);
                 m = __funnelshift_r(lo, hi, sh) & PR[t];
             }
             if (m) pm = 2u * (32u * t + __clz(m)) + 1u;
@@ -437,7 +438,7 @@ __device__ __forceinline__ uint32_t pern_first(const uint32_t *win, const uint32
             const bool valid = k < ke;
             uint32_t pm = 0;
             if (valid && n_lo + 2ull * k != 4ull) {
-                const uint32_t m = __funnelshift_r(win[w + KW - 1u], win[w + KW], lane) & PR0;
+                const uint32_t m = __funnelshift_r(wld(&win[w + KW - 1u], DS_PERN), wld(&win[w + KW], DS_PERN), lane) & PR0;
                 if (m) pm = 2u * __clz(m) + 1u;
             }
             if (pm) fold_pmin(pm, k - ks, prm, acc, ss);
@@ -470,7 +471,8 @@ __device__ __forceinline__ void pern_groups(OpenRing &rg, int warp, const uint32
         const unsigned long long n = n_lo + 2ull * k;
         uint32_t pm = 0;
         if (valid && n != 4ull) {
-            const uint32_t m = __funnelshift_r(win[g32 + KW - 1u], win[g32 + KW], lane) & PR0;
+            const uint32_t m =
+                __funnelshift_r(wld(&win[g32 + KW - 1u], DS_PERN), wld(&win[g32 + KW], DS_PERN), lane) & PR0;
             if (m) pm = 2u * __clz(m) + 1u;
         }
         if (pm) fold_pmin(pm, k - ks, prm, acc, ss);

@@ -8,7 +8,9 @@
 namespace gbk {
 
 // Ctrl::flags bits
-enum : uint32_t { F_COUNTEREX = 1u, F_SLOWCAP = 2u, F_OVERFLOW = 4u, F_INTERNAL = 8u };
+// (F_BOUNDS: a bounds check of a GB_DEBUG build failed; F_INTERNAL is raised
+// with it, so the call fails)
+enum : uint32_t { F_COUNTEREX = 1u, F_SLOWCAP = 2u, F_OVERFLOW = 4u, F_INTERNAL = 8u, F_BOUNDS = 16u };
 
 // Record key: (max_pmin << 40) | (2^40 - 1 - k_argmax), so one 64-bit
 // atomicMax keeps the largest p_min and, on ties, the smallest n.
@@ -34,7 +36,9 @@ struct __align__(16) Ctrl {
     unsigned int flags;
     unsigned int merge_done;
     unsigned long long work_ctr;       // serving: next work item
-    unsigned long long pad[3];
+    unsigned int dbg_site;             // GB_DEBUG builds: site of the first failed bounds check
+    unsigned int dbg_off;              //   and its byte offset in the dynamic shared memory
+    unsigned long long pad[2];
 };
 
 // Everything a launch needs to know about one call, kept in device memory so a
@@ -51,6 +55,9 @@ struct __align__(16) RangeParams {
     unsigned int p_max;
     unsigned int slow_cap_log2;
     unsigned int bk_prime0;            // primes with index >= this come from buckets
+    unsigned int dbg_lim;              // GB_DEBUG builds: window accesses allowed in the first
+                                       // dbg_lim bytes of dynamic shared memory (0 = all of it)
+    unsigned int dbg_pad;
     unsigned long long tile0;          // this launch processes tiles [tile0, tile_end)
     unsigned long long tile_end;
     const unsigned long long *bk_off;  // bucket of tile t: entries [bk_off[t-tile0], bk_off[t-tile0+1])

@@ -49,6 +49,15 @@ def test_every_declared_symbol_is_exported(lib):
     assert not missing, missing
 
 
+def test_checked_build_exports_the_same_boundary():
+    # the GB_DEBUG variant (bounds checks on the shared-memory window) is the
+    # same library with the checks compiled in
+    from paper_2603_07850_gb300 import build
+    dbg = ctypes.CDLL(build.build(debug=True))
+    missing = [n for n in declared_functions() if not hasattr(dbg, n)]
+    assert not missing, missing
+
+
 def test_binding_names_match_the_abi():
     from paper_2603_07850_gb300 import binding
     for n in declared_functions():
