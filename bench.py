@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default configuration")
     ap.add_argument("--option", action="append", default=[], metavar="KEY=VALUE",
                     help="set a library option before the run (repeatable; e.g. search_chunks=6)")
-    ap.add_argument("--no-extra", action="store_true", help="skip the C1, C3a and C4 figures")
+    ap.add_argument("--no-extra", action="store_true", help="skip the C1, C3a, C3b and C4 figures")
     ap.add_argument("--serve-requests", type=int, default=2000)
     return ap.parse_args()
 
@@ -398,8 +398,8 @@ def measure_plain(gb, lo, hi, ref, flush, torch, stream, res):
 
 
 def measure_extra(gb, torch, args):
-    """C1 and C3a throughput, and a shortened C4 serving run, each on a fresh
-    context (rank 0 only)."""
+    """C1, C3a and C3b throughput, and a shortened C4 serving run, each on a
+    fresh context (rank 0 only)."""
     from paper_2603_07850_gb300 import workloads as W
     import serve_bench
     extra = {}
@@ -429,6 +429,21 @@ def measure_extra(gb, torch, args):
         r = gb.gb_verify_range(c.lo, c.hi)
         walls.append(time.perf_counter() - t)
     extra["C3a"] = {"workload": "[1e18, 1e18 + 1e10)", "value": r["n_count"] / min(walls), "unit": "even_n/s",
+                    "call_s": min(walls), "max_pmin": r["max_pmin"], "status": r["status"],
+                    "tuned": {k: gb.gb_get_option(k) for k in ("tile_bits", "threads", "search_chunks", "builder_warps",
+                                                               "bucket_min", "bucket_chunk_tiles", "tier_b_min")}}
+    gb.gb_shutdown()
+    # C3b: [2^64 - 2^33, 2^64 - 2), base primes to 2^32 - 1, the same way
+    c = W.C3B
+    gb.gb_init(c.p_max, c.seg_bits)
+    gb.gb_set_option("autotune", 1)
+    gb.gb_verify_range(c.lo, c.hi)
+    walls = []
+    for _ in range(3):
+        t = time.perf_counter()
+        r = gb.gb_verify_range(c.lo, c.hi)
+        walls.append(time.perf_counter() - t)
+    extra["C3b"] = {"workload": "[2^64 - 2^33, 2^64 - 2)", "value": r["n_count"] / min(walls), "unit": "even_n/s",
                     "call_s": min(walls), "max_pmin": r["max_pmin"], "status": r["status"],
                     "tuned": {k: gb.gb_get_option(k) for k in ("tile_bits", "threads", "search_chunks", "builder_warps",
                                                                "bucket_min", "bucket_chunk_tiles", "tier_b_min")}}
