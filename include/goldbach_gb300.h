@@ -165,7 +165,7 @@ int gb_init(uint32_t p_max, uint32_t seg_bits);
  *   "use_graph"     1 = replay a captured CUDA graph (default), 0 = direct launches
  *   "slow_cap"      log2 of the slow-path candidate cap per n, 6..24 (default 24)
  *   "timeout_ms"    bound for device-side waits and gb_poll defaults (default 600000)
- *   "tier_b_min"    smallest prime crossed off lane-per-prime (default 16384)
+ *   "tier_b_min"    smallest prime crossed off lane-per-prime (default 8192)
  *   "plain_slice_bits" log2 window bits per CTA in the plain sieve kernel (default 18)
  *   "plain_search_chunks" search of the plain form: 0 = the per-n search kernel
  *                   writing a p_min array that a reduce kernel folds (default);

@@ -43,7 +43,7 @@ struct Options {
     int64_t ctas_per_sm = 0;       // 0 = as many as fit
     int64_t wheel = 13;
     int64_t pattern_max = 31;
-    int64_t tier_b_min = 16384;
+    int64_t tier_b_min = 8192;     // measured best at 10^10, 10^12 and 10^18 against 2^11 .. 2^16
     int64_t base_limit = 0;
     int64_t mem_budget_mb = 8192;
     int64_t plain_seg_bits = 26;
@@ -948,7 +948,7 @@ int maybe_autotune(CallPlan &cp)
         std::vector<std::pair<int64_t TuneCfg::*, std::vector<int64_t>>> axes = {
             {&TuneCfg::builder_warps, {0, 8, 12, 16}},       // single-role or pipelined kernel
             {&TuneCfg::search_chunks, {4, 6, 8}},
-            {&TuneCfg::tier_b_min, {4096, 16384, 65536}},
+            {&TuneCfg::tier_b_min, {4096, 8192, 16384, 65536}},
             {&TuneCfg::threads, {256, 512, 768, 1024}},         // 4, 2, 1 or 1 CTAs per SM
             {&TuneCfg::tile_bits, {15, 16, 17, 18, 19, 20, 21}}, // 2^21 never fits shared memory
             {&TuneCfg::wheel, {7, 13}},
