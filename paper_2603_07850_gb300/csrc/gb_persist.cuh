@@ -141,6 +141,35 @@ __device__ __forceinline__ uint32_t bulk_bound(const RangeParams &prm)
     return bb;
 }
 
+// The bit-parallel pass over one warp's words of the sub-record [ks, ke):
+// word (ks >> 5) + 32 NWARP gi + lane for gi = 0, 1, ...; PART selects the
+// statistics folded into acc.  With BW_SUMS it also stores each word's open
+// mask at mb[32 gi + lane] while gi < gmax.  Returns the number of groups.
+template <int NWARP, int SEARCH_BC, int PART>
+__device__ __forceinline__ uint32_t bulk_pass(const uint32_t *win, uint32_t KW, uint32_t ks, uint32_t ke, int warp,
+                                              bool ball, uint32_t bb, uint32_t one, uint32_t *mb, uint32_t gmax,
+                                              SubAcc &acc)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t wbeg = ks >> 5, wend = (ke + 31) >> 5;
+    uint32_t gi = 0;
+    for (uint32_t wb = wbeg + 32u * warp; wb < wend; wb += 32u * NWARP, gi++) {
+        const uint32_t w = wb + lane;
+        const bool inw = w < wend;
+        uint32_t valid = 0u;
+        if (inw) {
+            const uint32_t kw0 = 32u * w;
+            valid = (kw0 + 32u <= ke) ? 0xffffffffu : (0xffffffffu >> (32u - (ke - kw0)));
+        }
+        const uint32_t wl = w - wbeg;
+        const uint32_t wr = inw ? w : wend - 1u;
+        const uint32_t U = ball ? bulk_word<SEARCH_BC, true, PART>(win, wr, wl, KW, valid, bb, one, acc)
+                                : bulk_word<SEARCH_BC, false, PART>(win, wr, wl, KW, valid, bb, one, acc);
+        if ((PART & BW_SUMS) && gi < gmax) mb[32u * gi + lane] = U;
+    }
+    return gi;
+}
+
 // Search every n of a tile whose window is built, and reduce it into its
 // record(s).  Run by a group of NWARP warps (the whole CTA, BAR = 0, or the
 // searching warps of the pipelined kernel); `warp` and `gt` are the warp's
@@ -205,30 +234,23 @@ __device__ __forceinline__ void search_tile(const RangeParams &prm, unsigned lon
             tw = phase_warp(t, PH_WARP_TAIL, tw);
         } else {
             const uint32_t one = s.one;                       // 1, a value the compiler cannot see
-            const uint32_t wbeg = ks >> 5, wend = (ke + 31) >> 5;
-            uint32_t gi = 0;
-            for (uint32_t wb = wbeg + 32u * warp; wb < wend; wb += 32u * NWARP, gi++) {
-                const uint32_t w = wb + lane;
-                const bool inw = w < wend;
-                uint32_t valid = 0u;
-                if (inw) {
-                    const uint32_t kw0 = 32u * w;
-                    valid = (kw0 + 32u <= ke) ? 0xffffffffu : (0xffffffffu >> (32u - (ke - kw0)));
-                }
-                const uint32_t wl = w - wbeg;
-                const uint32_t wr = inw ? w : wend - 1u;
-                const uint32_t U = ball ? bulk_word<SEARCH_BC, true>(win, wr, wl, KW, valid, bb, one, acc)
-                                        : bulk_word<SEARCH_BC, false>(win, wr, wl, KW, valid, bb, one, acc);
-                if (gi < gmax) mb[32u * gi + lane] = U;
-            }
+            uint32_t gi = bulk_pass<NWARP, SEARCH_BC, BW_SUMS>(win, KW, ks, ke, warp, ball, bb, one, mb, gmax, acc);
             if (gi > gmax) {                                 // the host sized the slots too small
                 if (lane == 0) atomicOr(&ctrl->flags, F_INTERNAL);
                 gi = gmax;
             }
             __syncwarp();
             tw = phase_warp(t, PH_WARP_BULK, tw);
-            ring_groups<NWARP>(rg, mb, 0u, gi, wbeg + 32u * warp, win, PR, KW, n_lo, ks, i_start, prm, acc, ss, ctrl);
+            ring_groups<NWARP>(rg, mb, 0u, gi, (ks >> 5) + 32u * warp, win, PR, KW, n_lo, ks, i_start, prm, acc, ss,
+                               ctrl);
             ring_flush(rg, win, PR, KW, n_lo, ks, i_start, prm, acc, ss, ctrl);
+            // Every p_min the per-n walk found exceeds every bit-parallel one
+            // (it is above bb), so the warp's largest p_min comes from the
+            // bit-parallel pass only when the walk found none; then that pass
+            // runs again for the max alone.  At scale nearly every warp has
+            // open n, and the per-word max stays out of the main loop.
+            if (!__any_sync(GB_FULL_MASK, acc.mx > bb))
+                bulk_pass<NWARP, SEARCH_BC, BW_MAX>(win, KW, ks, ke, warp, ball, bb, one, mb, 0u, acc);
             tw = phase_warp(t, PH_WARP_TAIL, tw);
         }
         a.mx = acc.mx;

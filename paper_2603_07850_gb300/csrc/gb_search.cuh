@@ -185,7 +185,11 @@ struct SubShared {
 // integer multiply-add, issued on the FMA pipe beside the ALU pipe that runs
 // the funnel shifts and logic ops (the newly resolved bits nw are disjoint
 // from every plane, so the add is an OR).
-template <int BC, bool ALL>
+// The word statistics bulk_word folds into acc: the sums and the histogram
+// (BW_SUMS), the largest p_min and its smallest n (BW_MAX).
+enum : int { BW_SUMS = 1, BW_MAX = 2 };
+
+template <int BC, bool ALL, int PART = BW_SUMS | BW_MAX>
 __device__ __forceinline__ uint32_t bulk_word(const uint32_t *win, uint32_t w, uint32_t wl, uint32_t KW,
                                               uint32_t valid, uint32_t bb, uint32_t one, SubAcc &acc)
 {
@@ -236,29 +240,33 @@ __device__ __forceinline__ uint32_t bulk_word(const uint32_t *win, uint32_t w, u
     if (R) {
         // sum and sum of b * p over the word, plane by plane
         const uint32_t Bs[9] = {B0, B1, B2, B3, B4, B5, B6, B7, B8};
-        uint32_t s = 0, sb = 0;
+        if (PART & BW_SUMS) {
+            uint32_t s = 0, sb = 0;
 #pragma unroll
-        for (int j = 0; j < (BC > 4 ? 9 : 8); j++) {
-            s += __popc(Bs[j]) << j;
-            sb += bitpos_sum(Bs[j]) << j;
-        }
-        acc.sum += s;
-        acc.wsum += (unsigned long long)s * (32ull * wl + 1ull) + sb;
-        // histogram: bin = index of the highest plane that is set
-        uint32_t H = 0;
+            for (int j = 0; j < (BC > 4 ? 9 : 8); j++) {
+                s += __popc(Bs[j]) << j;
+                sb += bitpos_sum(Bs[j]) << j;
+            }
+            acc.sum += s;
+            acc.wsum += (unsigned long long)s * (32ull * wl + 1ull) + sb;
+            // histogram: bin = index of the highest plane that is set
+            uint32_t H = 0;
 #pragma unroll
-        for (int j = (BC > 4 ? 8 : 7); j >= 1; j--) {
-            acc.h[(j - 1) >> 1] += __popc(Bs[j] & ~H) << (16 * ((j - 1) & 1));
-            H |= Bs[j];
+            for (int j = (BC > 4 ? 8 : 7); j >= 1; j--) {
+                acc.h[(j - 1) >> 1] += __popc(Bs[j] & ~H) << (16 * ((j - 1) & 1));
+                H |= Bs[j];
+            }
         }
-        // max over the word and its smallest n
-        uint32_t cand = R, mx = 0;
+        if (PART & BW_MAX) {
+            // max over the word and its smallest n
+            uint32_t cand = R, mx = 0;
 #pragma unroll
-        for (int j = (BC > 4 ? 8 : 7); j >= 0; j--) {
-            const uint32_t t = cand & Bs[j];
-            if (t) { cand = t; mx |= 1u << j; }
+            for (int j = (BC > 4 ? 8 : 7); j >= 0; j--) {
+                const uint32_t t = cand & Bs[j];
+                if (t) { cand = t; mx |= 1u << j; }
+            }
+            acc.take_max(mx, 32u * wl + (uint32_t)(__ffs(cand) - 1));
         }
-        acc.take_max(mx, 32u * wl + (uint32_t)(__ffs(cand) - 1));
     }
     return valid & ~V;
 }
