@@ -73,12 +73,13 @@ struct GraphKey {
     uint32_t olist_wcap = 0, olist_ctas = 0;
     const void *aperm = nullptr;
     uint32_t aperm_len = 0;
+    const void *askew = nullptr;
     bool operator==(const GraphKey &o) const
     {
         return fn == o.fn && grid == o.grid && nt == o.nt && wheel == o.wheel &&
                merge_grid == o.merge_grid && clear_records == o.clear_records && smem == o.smem &&
                recs == o.recs && olist == o.olist && olist_wcap == o.olist_wcap && olist_ctas == o.olist_ctas &&
-               aperm == o.aperm && aperm_len == o.aperm_len;
+               aperm == o.aperm && aperm_len == o.aperm_len && askew == o.askew;
     }
 };
 
@@ -139,6 +140,7 @@ struct Ctx {
     // balanced order of the tier-A primes (see Tables::aperm) and what it was built for
     uint32_t *d_aperm = nullptr;
     uint32_t aperm_len = 0;
+    unsigned long long *d_askew = nullptr;    // tier-A lane skews (ASKEW_ENTRIES)
     uint64_t aperm_key[5] = {0, 0, 0, 0, 0};
     std::map<uint64_t, uint32_t> odd_primes_below;  // cache: bound -> #odd primes below it
     char dev_name[256] = {0};
@@ -332,6 +334,7 @@ Tables make_tables(int wheel)
     const bool aperm_fits = g.d_aperm && g.aperm_key[0] == t.iA0 && g.aperm_key[1] == t.iB0;
     t.aperm = aperm_fits ? g.d_aperm : nullptr;
     t.aperm_len = aperm_fits ? g.aperm_len : 0u;
+    t.askew = g.d_askew;
     t.phase = g.d_phase;
     return t;
 }
@@ -600,6 +603,75 @@ int ensure_olist(int grid, int nt, uint32_t tile_bits, bool bulk)
     return GB_OK;
 }
 
+// Lane skews of the tier-A marks.  In a warp-per-prime pass lane l marks the
+// multiples l, l + 32, ... of p: one warp step touches the words
+// floor((r + l p) / 32) + const, r = the first bit mod 32, and their
+// shared-memory banks (word mod 32) collide for many p.  Lane l may start at
+// its d_l-th multiple (d_l < 4) and mark its first d_l last, which moves its
+// bank by d_l p.  For each (p mod 1024, r) -- all the banks depend on -- the
+// d_l come from a bipartite matching of lanes to banks in which every bank
+// takes at most c lanes, c as small as possible, smaller d_l tried first
+// (augmenting paths, Kuhn 1955).  Entry ((p mod 1024) >> 1) * 32 + r holds d_l
+// in bits 2l, 2l + 1.  The marks are the same in any order.
+constexpr size_t ASKEW_ENTRIES = 512 * 32;
+
+struct SkewMatch {
+    int opt[32][4];
+    int cap;
+    int lanes[32][32], nl[32];               // lanes assigned to each bank
+    int choice[32];
+    bool seen[32];
+    bool aug(int l)
+    {
+        for (int d = 0; d < 4; d++) {
+            const int b = opt[l][d];
+            if (seen[b]) continue;
+            seen[b] = true;
+            if (nl[b] < cap) {
+                lanes[b][nl[b]++] = l;
+                choice[l] = d;
+                return true;
+            }
+            for (int i = 0; i < nl[b]; i++) {
+                if (aug(lanes[b][i])) {              // that lane moved to another bank
+                    lanes[b][i] = l;
+                    choice[l] = d;
+                    return true;
+                }
+            }
+        }
+        return false;
+    }
+};
+
+const std::vector<unsigned long long> &tier_a_skews()
+{
+    static std::vector<unsigned long long> tab;
+    if (!tab.empty()) return tab;
+    tab.assign(ASKEW_ENTRIES, 0ull);
+    for (uint32_t h = 0; h < 512; h++) {
+        const uint32_t p = 2 * h + 1;                // p mod 1024: the banks depend on nothing else
+        for (uint32_t r = 0; r < 32; r++) {
+            SkewMatch m;
+            for (int l = 0; l < 32; l++)
+                for (int d = 0; d < 4; d++) m.opt[l][d] = (int)((((r + (uint32_t)l * p) >> 5) + (uint32_t)d * p) & 31u);
+            for (m.cap = 1; m.cap <= 32; m.cap++) {
+                std::fill(m.nl, m.nl + 32, 0);
+                bool ok = true;
+                for (int l = 0; l < 32 && ok; l++) {
+                    std::fill(m.seen, m.seen + 32, false);
+                    ok = m.aug(l);
+                }
+                if (ok) break;
+            }
+            unsigned long long e = 0;
+            for (int l = 0; l < 32; l++) e |= (unsigned long long)m.choice[l] << (2 * l);
+            tab[h * 32 + r] = e;
+        }
+    }
+    return tab;
+}
+
 // The tier-A primes of the current tables spread over the warps of an
 // nt-thread CTA by longest processing time first: each prime, heaviest first,
 // goes to the least-loaded warp.  A prime's load is its crossing-off steps per
@@ -607,6 +679,12 @@ int ensure_olist(int grid, int nt, uint32_t tile_bits, bool bulk)
 // are exact with any order; this only evens out the warps' work.
 int ensure_aperm(int nt)
 {
+    if (!g.d_askew) {
+        const std::vector<unsigned long long> &sk = tier_a_skews();
+        int rc;
+        if ((rc = dev_alloc(&g.d_askew, 8ull * ASKEW_ENTRIES))) return rc;
+        CK(cudaMemcpy(g.d_askew, sk.data(), 8ull * ASKEW_ENTRIES, cudaMemcpyHostToDevice));
+    }
     const Tables t = make_tables();
     const uint64_t nwarp = (uint64_t)nt / 32;
     const uint64_t key[5] = {t.iA0, t.iB0, nwarp, (uint64_t)g.opt.tile_bits, g.k_words};
@@ -998,7 +1076,7 @@ int async_graph(const CallPlan &cp, const RangeParams &p, gb_result *dev_out, in
     key.merge_grid = mg; key.clear_records = g.opt.tile_bits < g.seg_bits ? 1 : 0; key.smem = smem;
     key.recs = g.d_recs; key.olist = g.d_olist; key.olist_wcap = g.olist_wcap; key.olist_ctas = g.olist_ctas;
     const Tables tk = make_tables();
-    key.aperm = tk.aperm; key.aperm_len = tk.aperm_len;
+    key.aperm = tk.aperm; key.aperm_len = tk.aperm_len; key.askew = tk.askew;
     if (!g.aexec || !(key == g.akey) || g.aout != dev_out) {
         if (g.aexec) { cudaGraphExecDestroy(g.aexec); g.aexec = nullptr; }
         if (g.agraph) { cudaGraphDestroy(g.agraph); g.agraph = nullptr; }
@@ -1077,7 +1155,7 @@ int run_persistent(uint64_t lo, uint64_t hi, CallPlan &cp)
         key.clear_records = clear_records; key.smem = smem; key.recs = g.d_recs;
         key.olist = g.d_olist; key.olist_wcap = g.olist_wcap; key.olist_ctas = g.olist_ctas;
         const Tables tk = make_tables();
-        key.aperm = tk.aperm; key.aperm_len = tk.aperm_len;
+        key.aperm = tk.aperm; key.aperm_len = tk.aperm_len; key.askew = tk.askew; key.askew = tk.askew;
         if (!(key == g.gkey) || !g.gexec) {
             if (g.gexec) { cudaGraphExecDestroy(g.gexec); g.gexec = nullptr; }
             cudaGraph_t graph = nullptr;
@@ -1266,6 +1344,7 @@ void release_all()
     dev_free(&g.d_bk_ent, 4 * g.bk_ent_cap);
     dev_free(&g.d_olist, 4 * g.olist_cap);
     dev_free(&g.d_aperm, 4ull * g.aperm_len);
+    dev_free(&g.d_askew, 8ull * ASKEW_ENTRIES);
     dev_free(&g.d_phase, 8ull * PH_COUNT);
     if (g.h_params) cudaFreeHost(g.h_params);
     if (g.h_result) cudaFreeHost(g.h_result);

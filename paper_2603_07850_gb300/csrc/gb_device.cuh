@@ -567,6 +567,19 @@ __device__ __forceinline__ void mark_words(uint32_t *win, uint32_t w, uint32_t w
     for (; w < w_end; w += p) wand(&win[w], m, DS_MARK_A);
 }
 
+// Tier-A primes below this bound get the lane skews (measured: 512 and 1024
+// alike, 2048 and all primes slower).
+constexpr uint32_t SKEW_PMAX = 1024;
+
+// The same for a lane that starts at its d-th multiple w + d p and takes the
+// first d (w, w + p, ...) last: the same marks in another order.
+__device__ __forceinline__ void mark_words_skew(uint32_t *win, uint32_t w, uint32_t w_end, uint32_t p, uint32_t m,
+                                                uint32_t d)
+{
+    mark_words(win, w + d * p, w_end, p, m);
+    for (uint32_t k = 0; k < d && w < w_end; k++, w += p) wand(&win[w], m, DS_MARK_A);
+}
+
 __device__ __forceinline__ void clear_bit(uint32_t *win, uint32_t j)
 {
     // ~(1 << (j mod 32)) as one rotate: a funnel shift of 0xfffffffe with itself
@@ -587,6 +600,12 @@ __device__ __forceinline__ void mark_pass(uint32_t *win, const WinGeom &g, const
     // w takes every NWARP-th entry of the prime order (balanced by the host,
     // else the ascending primes), 32 at a time: lane q finds the first
     // multiple of the q-th, then the warp marks the 32 primes in turn.
+    // The 32 words of one warp step, floor((r + l p) / 32) + const (r = the
+    // first bit mod 32), often share shared-memory banks; for p < SKEW_PMAX
+    // lane l then starts at its d_l-th multiple (d_l < 4, from the host's
+    // table for p mod 1024 and r), which moves its bank by d_l p, and marks
+    // its first d_l last.  A larger p has too few marks per lane: the
+    // reordered tails cost more than the conflicts they save.
     const uint32_t a_end = t.iB0 < np ? t.iB0 : np;
     unsigned long long tw = phase_warp(t, -1, 0ull);
     // batch entry e of this warp (lane q holds entry e0 + q NWARP): a prime
@@ -598,16 +617,27 @@ __device__ __forceinline__ void mark_pass(uint32_t *win, const WinGeom &g, const
         const bool in = iq < a_end;
         const uint32_t pq = in ? t.primes[iq] : 0u;
         const uint32_t jq = in ? first_bit(g, pq, t.recip[iq]) : 0xffffffffu;
+        const unsigned long long sq = t.askew && jq != 0xffffffffu && pq < SKEW_PMAX
+                                          ? t.askew[(((pq & 1023u) >> 1) << 5) | (jq & 31u)] : 0ull;
+        const bool bskew = __any_sync(GB_FULL_MASK, sq != 0ull);  // some prime of the batch is skewed
         const uint32_t nq = (e_end - e0 + NWARP - 1) / NWARP;   // entries of this batch
         for (uint32_t q = 0; q < nq && q < 32u; q++) {
             const uint32_t j0 = __shfl_sync(GB_FULL_MASK, jq, q);
             if (j0 == 0xffffffffu) continue;
             const uint32_t p = __shfl_sync(GB_FULL_MASK, pq, q);
+            uint32_t d = 0;
+            if (bskew) {
+                const uint32_t s_lo = __shfl_sync(GB_FULL_MASK, (uint32_t)sq, q);
+                const uint32_t s_hi = __shfl_sync(GB_FULL_MASK, (uint32_t)(sq >> 32), q);
+                d = ((lane < 16 ? s_lo : s_hi) >> (2u * (lane & 15u))) & 3u;
+            }
             const uint32_t jl = j0 + lane * p;              // j0 < 2^21, p < 2^16: no wrap
             if (jl >= j_end) continue;
             const uint32_t b = jl & 31u;
-            mark_words(win, jl >> 5, (j_end - b + 31u) >> 5,  // words w with 32 w + b < j_end
-                       p, __funnelshift_l(0xfffffffeu, 0xfffffffeu, b));
+            const uint32_t w_end = (j_end - b + 31u) >> 5;  // words w with 32 w + b < j_end
+            const uint32_t m = __funnelshift_l(0xfffffffeu, 0xfffffffeu, b);
+            if (bskew) mark_words_skew(win, jl >> 5, w_end, p, m, d);
+            else mark_words(win, jl >> 5, w_end, p, m);
         }
     }
     tw = phase_warp(t, PH_WARP_TIER_A, tw);

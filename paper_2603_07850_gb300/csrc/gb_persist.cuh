@@ -153,6 +153,11 @@ __device__ __forceinline__ uint32_t bulk_pass(const uint32_t *win, uint32_t KW, 
     const int lane = threadIdx.x & 31;
     const uint32_t wbeg = ks >> 5, wend = (ke + 31) >> 5;
     uint32_t gi = 0;
+    // with BW_SUMS the pass starts with acc's sums at zero: it adds the sum
+    // of p over its words to acc.sum, sum_b b T(b) to acc.wsum, and the word
+    // weights at the end
+    PosAcc pa;
+    pa.G = 0u;
     for (uint32_t wb = wbeg + 32u * warp; wb < wend; wb += 32u * NWARP, gi++) {
         const uint32_t w = wb + lane;
         const bool inw = w < wend;
@@ -163,9 +168,20 @@ __device__ __forceinline__ uint32_t bulk_pass(const uint32_t *win, uint32_t KW, 
         }
         const uint32_t wl = w - wbeg;
         const uint32_t wr = inw ? w : wend - 1u;
-        const uint32_t U = ball ? bulk_word<SEARCH_BC, true, PART>(win, wr, wl, KW, valid, bb, one, acc)
-                                : bulk_word<SEARCH_BC, false, PART>(win, wr, wl, KW, valid, bb, one, acc);
-        if ((PART & BW_SUMS) && gi < gmax) mb[32u * gi + lane] = U;
+        const uint32_t U = ball ? bulk_word<SEARCH_BC, true, PART>(win, wr, wl, gi, KW, valid, bb, one, acc, pa)
+                                : bulk_word<SEARCH_BC, false, PART>(win, wr, wl, gi, KW, valid, bb, one, acc, pa);
+        if (PART & BW_SUMS) {
+            if (gi < gmax) mb[32u * gi + lane] = U;
+            if ((gi & (PosAcc::CAP - 1u)) == PosAcc::CAP - 1u) pos_flush(pa, PosAcc::CAP, acc);
+        }
+    }
+    if (PART & BW_SUMS) {
+        // words since the last flush
+        if (gi & (PosAcc::CAP - 1u)) pos_flush(pa, gi & (PosAcc::CAP - 1u), acc);
+        // word gi of this lane is wl = wl0 + 32 NWARP gi: its n weigh
+        // 32 wl + b + 1 = (32 wl0 + 1) + 1024 NWARP gi + b
+        const uint32_t wl0 = 32u * (uint32_t)warp + (uint32_t)lane;
+        acc.wsum += acc.sum * (32ull * wl0 + 1ull) + (unsigned long long)pa.G * (1024ull * NWARP);
     }
     return gi;
 }

@@ -176,29 +176,69 @@ struct SubShared {
     unsigned long long *ce;                 // max ~n over counterexamples
 };
 
+// Bit-sliced sums of p_min per bit position over the words a lane has folded
+// since the last flush: plane j of T holds bit j of sum_w p_w(b) for every bit
+// position b (p_w(b) = p_min of n 32 w + b, 0 when open).  A word adds its
+// nine bit planes with a ripple of three-input logic ops, so the position
+// weights of wsum cost popcounts once per flush instead of once per word
+// (sum_b b p(b) is what wsum needs beyond the per-word sum).  Every p_min of
+// the bulk phase is below 512, so CAP = 2^(TW - 9) words never overflow the
+// TW planes.
+constexpr int POS_TW = 12;
+struct PosAcc {
+    uint32_t T[POS_TW];
+    uint32_t G;                             // sum over the pass's words of gi * (sum of p over word gi)
+    static constexpr uint32_t CAP = 1u << (POS_TW - 9);
+};
+
+// Fold sum_b b T(b) of the nw words in pa into acc.wsum.  Plane j can be set
+// only when nw * 511 >= 2^j.
+__device__ __forceinline__ void pos_flush(const PosAcc &pa, uint32_t nw, SubAcc &acc)
+{
+    uint32_t sb = 0;                        // <= 496 * 2^POS_TW: no wrap
+#pragma unroll
+    for (int j = 0; j < POS_TW; j++)
+        if (j < 9 || nw > (1u << (j - 9))) sb += bitpos_sum(pa.T[j]) << j;
+    acc.wsum += sb;
+}
+
 // One word of the bulk phase: resolves candidates p < 64 BC with p <= bb,
-// folds the resolved bits into acc and returns the still-open bits.  bb never
-// exceeds P_max, so nothing resolved here counts towards n_slow.  ALL = every
-// candidate below 64 BC is <= bb (the usual case), so no candidate is tested
-// against bb at run time.
+// folds the resolved bits into acc and pa (word gi of the lane's pass, wl =
+// its index in the sub-record) and returns the still-open bits.  bb never exceeds P_max, so nothing resolved here
+// counts towards n_slow.  ALL = every candidate below 64 BC is <= bb (the
+// usual case), so no candidate is tested against bb at run time.
 // `one` is 1, passed at run time: a plane update B += nw * one is then an
 // integer multiply-add, issued on the FMA pipe beside the ALU pipe that runs
 // the funnel shifts and logic ops (the newly resolved bits nw are disjoint
 // from every plane, so the add is an OR).
-// The word statistics bulk_word folds into acc: the sums and the histogram
-// (BW_SUMS), the largest p_min and its smallest n (BW_MAX).
+// The word statistics bulk_word folds: the sums and the histogram (BW_SUMS),
+// the largest p_min and its smallest n (BW_MAX).
 enum : int { BW_SUMS = 1, BW_MAX = 2 };
 
+// Histogram bin b (1..8) of acc gains v.
+__device__ __forceinline__ void hist_add(SubAcc &acc, int b, uint32_t v)
+{
+    acc.h[(b - 1) >> 1] += v << (16 * ((b - 1) & 1));
+}
+
 template <int BC, bool ALL, int PART = BW_SUMS | BW_MAX>
-__device__ __forceinline__ uint32_t bulk_word(const uint32_t *win, uint32_t w, uint32_t wl, uint32_t KW,
-                                              uint32_t valid, uint32_t bb, uint32_t one, SubAcc &acc)
+__device__ __forceinline__ uint32_t bulk_word(const uint32_t *win, uint32_t w, uint32_t wl, uint32_t gi,
+                                              uint32_t KW, uint32_t valid, uint32_t bb, uint32_t one,
+                                              SubAcc &acc, PosAcc &pa)
 {
     // Every candidate is odd, so plane 0 collects exactly the resolved bits:
     // it doubles as the "already resolved" mask (invalid bits start set).
     // The candidates of one 32-wide range of p share the bits of p from bit 5
     // up, so planes 5.. take the bits the range resolved once, after it; each
     // candidate adds its newly resolved bits only to planes 1..4.
+    // Candidates run in ascending order, so the n of histogram bin b (p_min in
+    // [2^b, 2^(b+1))) are those resolved between the candidate boundaries 2^b
+    // and 2^(b+1): with BW_SUMS each bin is the difference of two popcounts of
+    // B0 taken at those boundaries.
+    constexpr bool SUMS = (PART & BW_SUMS) != 0;
     uint32_t B0 = ~valid, B1 = 0, B2 = 0, B3 = 0, B4 = 0, B5 = 0, B6 = 0, B7 = 0, B8 = 0;
+    const uint32_t c0 = SUMS ? (uint32_t)__popc(B0) : 0u;
+    uint32_t cp = c0;                                 // popcount of B0 at the last bin boundary
 #pragma unroll
     for (int c = 0; c < BC; c++) {
         // a chunk past the window's K bits holds no candidate <= bb (only
@@ -224,6 +264,12 @@ __device__ __forceinline__ uint32_t bulk_word(const uint32_t *win, uint32_t w, u
                     if (p & 16u) B4 = nw * one + B4;
                     B0 |= x;
                 }
+                // bins 1, 2, 3 end after the candidates 3, 7 and 13 (range 0)
+                if (SUMS && g == 0u && (p == 3u || p == 7u || p == 13u)) {
+                    const uint32_t cn = __popc(B0);
+                    hist_add(acc, p == 3u ? 1 : p == 7u ? 2 : 3, cn - cp);
+                    cp = cn;
+                }
             }
             if (g != 0u) {
                 const uint32_t D = B0 & ~B_start;       // resolved by this range
@@ -232,33 +278,53 @@ __device__ __forceinline__ uint32_t bulk_word(const uint32_t *win, uint32_t w, u
                 if ((32u * g) & 128u) B7 = D * one + B7;
                 if ((32u * g) & 256u) B8 = D * one + B8;
             }
+            // bins 4.. end with the ranges g = 2^(b-4) - 1; the last bin
+            // with candidates ends with the loop
+            if (SUMS && (g == 0u || g == 1u || g == 3u || g == 7u || g == 15u || g + 1u == 2u * BC)) {
+                const uint32_t cn = __popc(B0);
+                hist_add(acc, g == 0u ? 4 : 5 + (31 - __clz(g)), cn - cp);
+                cp = cn;
+            }
         }
     }
     const uint32_t V = B0;
     B0 &= valid;
-    const uint32_t R = V & valid;                     // resolved n of this word
-    if (R) {
-        // sum and sum of b * p over the word, plane by plane
+    if (SUMS) {
+        // sum over the word, plane by plane (plane 0 has cp - c0 bits)
+        constexpr int NPL = BC > 4 ? 9 : 8;
         const uint32_t Bs[9] = {B0, B1, B2, B3, B4, B5, B6, B7, B8};
-        if (PART & BW_SUMS) {
-            uint32_t s = 0, sb = 0;
+        uint32_t s = cp - c0;
 #pragma unroll
-            for (int j = 0; j < (BC > 4 ? 9 : 8); j++) {
-                s += __popc(Bs[j]) << j;
-                sb += bitpos_sum(Bs[j]) << j;
-            }
-            acc.sum += s;
-            acc.wsum += (unsigned long long)s * (32ull * wl + 1ull) + sb;
-            // histogram: bin = index of the highest plane that is set
-            uint32_t H = 0;
+        for (int j = 1; j < NPL; j++) s += __popc(Bs[j]) << j;
+        acc.sum += s;
+        pa.G += gi * s;
+        // the position-weighted part: add the planes to pa (the first word
+        // after a flush starts it)
+        if ((gi & (PosAcc::CAP - 1u)) == 0u) {
 #pragma unroll
-            for (int j = (BC > 4 ? 8 : 7); j >= 1; j--) {
-                acc.h[(j - 1) >> 1] += __popc(Bs[j] & ~H) << (16 * ((j - 1) & 1));
-                H |= Bs[j];
+            for (int j = 0; j < POS_TW; j++) pa.T[j] = j < NPL ? Bs[j] : 0u;
+        } else {
+            uint32_t cy = pa.T[0] & B0;
+            pa.T[0] ^= B0;
+#pragma unroll
+            for (int j = 1; j < POS_TW; j++) {
+                const uint32_t t = pa.T[j];
+                if (j < NPL) {
+                    const uint32_t x = Bs[j];
+                    pa.T[j] = t ^ x ^ cy;
+                    cy = (t & x) | (cy & (t ^ x));
+                } else {
+                    pa.T[j] = t ^ cy;
+                    cy = t & cy;
+                }
             }
         }
-        if (PART & BW_MAX) {
+    }
+    if (PART & BW_MAX) {
+        const uint32_t R = V & valid;                 // resolved n of this word
+        if (R) {
             // max over the word and its smallest n
+            const uint32_t Bs[9] = {B0, B1, B2, B3, B4, B5, B6, B7, B8};
             uint32_t cand = R, mx = 0;
 #pragma unroll
             for (int j = (BC > 4 ? 8 : 7); j >= 0; j--) {

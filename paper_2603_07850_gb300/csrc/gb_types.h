@@ -108,6 +108,9 @@ struct Tables {
     // balanced by work; null = round-robin over the ascending primes
     const uint32_t *aperm;
     uint32_t aperm_len;
+    // lane skews of the tier-A marks (2 bits a lane) by ((p mod 1024) >> 1,
+    // first bit mod 32): 512 x 32 entries; null = no skew
+    const unsigned long long *askew;
     // per-phase clock64 sums of builds with GB_PHASE_CLOCKS defined (slots
     // PH_*), null otherwise
     unsigned long long *phase;
