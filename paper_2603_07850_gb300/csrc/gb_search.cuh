@@ -7,14 +7,17 @@
 // 32 n per instruction).  A lane owns one word and walks the odd primes
 // p < 64 BC (BC <= 8, so p < 512) in ascending order (compile-time unrolled);
 // each candidate resolves the bits that are still open:
-//     x  = funnelshift(window words);  nw = x & ~V;  V |= x;
-// and records p in bit-sliced form (plane j gets nw when bit j of p is 1;
-// planes 5.. once per 32-wide range of candidates).  The record statistics of
-// the word then come from the planes with popcounts: sum, wsum, the log2
-// histogram and the max with its smallest n.  The few n left open
-// (p_min >= 64 BC) are compacted through a per-warp shared ring into full
-// rounds of 32 and finish with the per-n search from chunk BC on, then the
-// exact slow path.
+//     x = funnelshift(window words);  V |= x;
+// and p is recorded in bit-sliced form: plane j holds the n whose p_min has
+// bit j set.  V only gains bits, so the n a run of consecutive candidates
+// resolved are V(after the run) - V(before it); plane j adds that difference
+// once per run of candidates with bit j set (bits 1..4 of p), and planes 5..
+// once per 32-wide range of candidates.  The record statistics come from the
+// planes: the sums through bit-sliced per-position accumulators, the log2
+// histogram from popcounts of V at the candidate boundaries 2^b, and the max
+// with its smallest n.  The few n left open (p_min >= 64 BC) are compacted
+// through a per-warp shared ring into full rounds of 32 and finish with the
+// per-n search from chunk BC on, then the exact slow path.
 #pragma once
 #include "gb_device.cuh"
 
@@ -204,13 +207,16 @@ __device__ __forceinline__ void pos_flush(const PosAcc &pa, uint32_t nw, SubAcc 
 
 // One word of the bulk phase: resolves candidates p < 64 BC with p <= bb,
 // folds the resolved bits into acc and pa (word gi of the lane's pass, wl =
-// its index in the sub-record) and returns the still-open bits.  bb never exceeds P_max, so nothing resolved here
-// counts towards n_slow.  ALL = every candidate below 64 BC is <= bb (the
-// usual case), so no candidate is tested against bb at run time.
-// `one` is 1, passed at run time: a plane update B += nw * one is then an
-// integer multiply-add, issued on the FMA pipe beside the ALU pipe that runs
-// the funnel shifts and logic ops (the newly resolved bits nw are disjoint
-// from every plane, so the add is an OR).
+// its index in the sub-record) and returns the still-open bits.  bb never
+// exceeds P_max, so nothing resolved here counts towards n_slow.  ALL = every
+// candidate below 64 BC is <= bb (the usual case), so no candidate is tested
+// against bb at run time.
+// `one` is 1 and `mone` -1, passed at run time: a run's plane update
+// B += V_end - V_start is then two integer multiply-adds, issued on the FMA
+// pipe beside the ALU pipe that runs the funnel shifts and the ORs (the loop
+// is bound by the ALU pipe; plane 3 takes a three-input add on it, which
+// measured best).  The difference holds no bit of any plane, so the add is
+// an OR.
 // The word statistics bulk_word folds: the sums and the histogram (BW_SUMS),
 // the largest p_min and its smallest n (BW_MAX).
 enum : int { BW_SUMS = 1, BW_MAX = 2 };
@@ -227,10 +233,11 @@ __device__ __forceinline__ uint32_t bulk_word(const uint32_t *win, uint32_t w, u
                                               SubAcc &acc, PosAcc &pa)
 {
     // Every candidate is odd, so plane 0 collects exactly the resolved bits:
-    // it doubles as the "already resolved" mask (invalid bits start set).
+    // it doubles as the "already resolved" mask V (invalid bits start set).
     // The candidates of one 32-wide range of p share the bits of p from bit 5
-    // up, so planes 5.. take the bits the range resolved once, after it; each
-    // candidate adds its newly resolved bits only to planes 1..4.
+    // up, so planes 5.. take the bits the range resolved once, after it;
+    // planes 1..4 take theirs once per run of candidates (Rj = B0 where the
+    // run of plane j began).
     // Candidates run in ascending order, so the n of histogram bin b (p_min in
     // [2^b, 2^(b+1))) are those resolved between the candidate boundaries 2^b
     // and 2^(b+1): with BW_SUMS each bin is the difference of two popcounts of
@@ -239,6 +246,8 @@ __device__ __forceinline__ uint32_t bulk_word(const uint32_t *win, uint32_t w, u
     uint32_t B0 = ~valid, B1 = 0, B2 = 0, B3 = 0, B4 = 0, B5 = 0, B6 = 0, B7 = 0, B8 = 0;
     const uint32_t c0 = SUMS ? (uint32_t)__popc(B0) : 0u;
     uint32_t cp = c0;                                 // popcount of B0 at the last bin boundary
+    uint32_t R1 = 0, R2 = 0, R3 = 0, R4 = 0;          // B0 where the open run of plane j began
+    const uint32_t mone = 0u - one;
 #pragma unroll
     for (int c = 0; c < BC; c++) {
         // a chunk past the window's K bits holds no candidate <= bb (only
@@ -255,14 +264,19 @@ __device__ __forceinline__ uint32_t bulk_word(const uint32_t *win, uint32_t w, u
             for (int ci = 0; ci < cand_count(BC); ci++) {
                 const uint32_t p = cand_prime(ci);
                 const uint32_t i = (p - 1) >> 1;
-                if ((p >> 5) == g && (ALL || p <= bb)) {
-                    const uint32_t x = __funnelshift_r(lo, hi, 31u - (i & 31u));
-                    const uint32_t nw = x & ~B0;        // newly resolved
-                    if (p & 2u) B1 = nw * one + B1;
-                    if (p & 4u) B2 = nw * one + B2;
-                    if (p & 8u) B3 = nw * one + B3;
-                    if (p & 16u) B4 = nw * one + B4;
-                    B0 |= x;
+                if ((p >> 5) == g) {
+                    // the candidates of this range just before and after p
+                    const uint32_t pv = ci > 0 && (cand_prime(ci - 1) >> 5) == g ? cand_prime(ci - 1) : 0u;
+                    const uint32_t pn = (cand_prime(ci + 1) >> 5) == g ? cand_prime(ci + 1) : 0u;
+                    if ((p & 2u) && !(pv & 2u)) R1 = B0;
+                    if ((p & 4u) && !(pv & 4u)) R2 = B0;
+                    if ((p & 8u) && !(pv & 8u)) R3 = B0;
+                    if ((p & 16u) && !(pv & 16u)) R4 = B0;
+                    if (ALL || p <= bb) B0 |= __funnelshift_r(lo, hi, 31u - (i & 31u));
+                    if ((p & 2u) && !(pn & 2u)) B1 = R1 * mone + (B0 * one + B1);
+                    if ((p & 4u) && !(pn & 4u)) B2 = R2 * mone + (B0 * one + B2);
+                    if ((p & 8u) && !(pn & 8u)) B3 = B3 + B0 - R3;
+                    if ((p & 16u) && !(pn & 16u)) B4 = R4 * mone + (B0 * one + B4);
                 }
                 // bins 1, 2, 3 end after the candidates 3, 7 and 13 (range 0)
                 if (SUMS && g == 0u && (p == 3u || p == 7u || p == 13u)) {
