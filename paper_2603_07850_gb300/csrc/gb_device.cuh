@@ -473,11 +473,17 @@ __device__ __forceinline__ uint32_t pattern_phase(const WinGeom &g, uint32_t M)
     return (uint32_t)((u0 + 32ull * threadIdx.x) % M);
 }
 
-// The fill loop; REG = some primes are cleared by in-register masks.
-template <int WHEEL, int NT, bool REG>
+// The fill loop; REG = some primes are cleared by in-register masks, GROUPS =
+// group patterns applied.  Only the words at the window's two edges take
+// the masks of [clear_upto, j_end).
+template <int WHEEL, int NT, bool REG, int GROUPS>
 __device__ __forceinline__ void fill_words(uint32_t *win, const uint32_t *wpat, const WinGeom &g,
-                                           uint32_t pat_lo, uint32_t pat_hi, bool use1, bool use2)
+                                           uint32_t pat_lo, uint32_t pat_hi)
 {
+    constexpr bool use1 = GROUPS >= 1, use2 = GROUPS >= 2;
+    // words fully inside [clear_upto, j_end) need no edge mask
+    const uint32_t w_lo = (g.clear_upto + 31u) >> 5, w_hi = g.j_end >> 5;
+    const uint32_t nint = w_hi > w_lo ? w_hi - w_lo : 0u;
     constexpr uint32_t M = WheelM<WHEEL>::M;
     constexpr uint32_t STEP_M = (32u * NT) % M;
     constexpr uint32_t STEP_1 = (32u * NT) % G1_M, STEP_2 = (32u * NT) % G2_M;
@@ -514,9 +520,11 @@ __device__ __forceinline__ void fill_words(uint32_t *win, const uint32_t *wpat, 
                 }
             }
         }
-        uint32_t jw = 32u * w;
-        if (jw + 32 > g.j_end) word &= (g.j_end > jw) ? (0xffffffffu >> (32 - (g.j_end - jw))) : 0u;
-        if (g.clear_upto > jw) word &= (g.clear_upto >= jw + 32) ? 0u : (0xffffffffu << (g.clear_upto - jw));
+        if (w - w_lo >= nint) {
+            const uint32_t jw = 32u * w;
+            if (jw + 32 > g.j_end) word &= (g.j_end > jw) ? (0xffffffffu >> (32 - (g.j_end - jw))) : 0u;
+            if (g.clear_upto > jw) word &= (g.clear_upto >= jw + 32) ? 0u : (0xffffffffu << (g.clear_upto - jw));
+        }
         wst(&win[w], word, DS_FILL);
         u += STEP_M;
         if (u >= M) u -= M;
@@ -532,9 +540,16 @@ template <int WHEEL, int NT>
 __device__ __forceinline__ void fill_pass(uint32_t *win, const uint32_t *wpat, const WinGeom &g,
                                           uint32_t pat_lo, uint32_t pat_hi, uint32_t groups)
 {
-    const bool use1 = WHEEL == 13 && groups >= 1, use2 = WHEEL == 13 && groups >= 2;
-    if (pat_lo < pat_hi) fill_words<WHEEL, NT, true>(win, wpat, g, pat_lo, pat_hi, use1, use2);
-    else fill_words<WHEEL, NT, false>(win, wpat, g, pat_lo, pat_hi, use1, use2);
+    const uint32_t gr = WHEEL == 13 ? groups : 0u;
+    if (pat_lo < pat_hi) {
+        if (gr >= 2) fill_words<WHEEL, NT, true, 2>(win, wpat, g, pat_lo, pat_hi);
+        else if (gr == 1) fill_words<WHEEL, NT, true, 1>(win, wpat, g, pat_lo, pat_hi);
+        else fill_words<WHEEL, NT, true, 0>(win, wpat, g, pat_lo, pat_hi);
+    } else {
+        if (gr >= 2) fill_words<WHEEL, NT, false, 2>(win, wpat, g, pat_lo, pat_hi);
+        else if (gr == 1) fill_words<WHEEL, NT, false, 1>(win, wpat, g, pat_lo, pat_hi);
+        else fill_words<WHEEL, NT, false, 0>(win, wpat, g, pat_lo, pat_hi);
+    }
 }
 
 // First window bit of the odd multiples of p that are >= max(p^2, wbase).
@@ -555,14 +570,26 @@ __device__ __forceinline__ uint32_t first_bit(const WinGeom &g, uint32_t p, unsi
     return j < g.j_end ? (uint32_t)j : 0xffffffffu;
 }
 
-// Clear mask m in words w, w + p, ... below w_end (unrolled by four).
+// Clear mask m in words w, w + p, ... below w_end (unrolled by eight, then
+// four: marks in flight per lane keep the shared-memory atomics busy).
 __device__ __forceinline__ void mark_words(uint32_t *win, uint32_t w, uint32_t w_end, uint32_t p, uint32_t m)
 {
-    for (; w + 3u * p < w_end; w += 4u * p) {
+    for (; w + 7u * p < w_end; w += 8u * p) {
         wand(&win[w], m, DS_MARK_A);
         wand(&win[w + p], m, DS_MARK_A);
         wand(&win[w + 2u * p], m, DS_MARK_A);
         wand(&win[w + 3u * p], m, DS_MARK_A);
+        wand(&win[w + 4u * p], m, DS_MARK_A);
+        wand(&win[w + 5u * p], m, DS_MARK_A);
+        wand(&win[w + 6u * p], m, DS_MARK_A);
+        wand(&win[w + 7u * p], m, DS_MARK_A);
+    }
+    if (w + 3u * p < w_end) {
+        wand(&win[w], m, DS_MARK_A);
+        wand(&win[w + p], m, DS_MARK_A);
+        wand(&win[w + 2u * p], m, DS_MARK_A);
+        wand(&win[w + 3u * p], m, DS_MARK_A);
+        w += 4u * p;
     }
     for (; w < w_end; w += p) wand(&win[w], m, DS_MARK_A);
 }
