@@ -626,7 +626,14 @@ int ensure_aperm(int nt)
         const std::vector<unsigned long long> &sk = tier_a_skews();
         int rc;
         if ((rc = dev_alloc(&g.d_askew, 8ull * ASKEW_ENTRIES))) return rc;
-        CK(cudaMemcpy(g.d_askew, sk.data(), 8ull * ASKEW_ENTRIES, cudaMemcpyHostToDevice));
+        auto upload = [&]() -> int {
+            CK(cudaMemcpy(g.d_askew, sk.data(), 8ull * ASKEW_ENTRIES, cudaMemcpyHostToDevice));
+            return GB_OK;
+        };
+        if ((rc = upload())) {                  // no half-written table: the next call uploads again
+            dev_free(&g.d_askew, 8ull * ASKEW_ENTRIES);
+            return rc;
+        }
     }
     const Tables t = make_tables();
     const uint64_t nwarp = (uint64_t)nt / 32;
